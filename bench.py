@@ -1,0 +1,362 @@
+"""Benchmark: GTEPS of the hybrid-transfer engine at a capped device budget.
+
+Workload (one "step"): on an R-MAT scale-24 graph (16,777,216 vertices,
+268,435,456 directed edges, a=0.57 b=0.19 c=0.19 d=0.05, seed 1, uint32
+weights uniform in [1, 64]) whose edge arrays live in pinned host memory,
+with a device budget of 25 % of the graph bytes: BFS and SSSP from vertex 0,
+connected components on the symmetrised graph (536,870,912 edges) and
+delta-PageRank (damping 0.85, FP32 residual threshold 1e-9), each to
+convergence through the C ABI.
+
+value  = edges relaxed (sum over iterations of active out-edges) / device
+         time of the runs (CUDA events on the library's main stream, which
+         joins all of its streams), summed over the K timed steps, over all
+         ranks, divided by the slowest rank's time;
+e2e    = the same edges over host wall time of hytg_run + hytg_fetch_result
+         (the public calls), including the result copies to host memory.
+
+Multi-GPU: replicas only (each rank runs the whole workload on its own GPU;
+no data-path collective); the barrier and max-over-ranks timing use
+torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS at capped device budget; host-link GB/s % of measured; batched vs plain"
+ALGOS = ["bfs", "sssp", "cc", "pagerank"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--budget-frac", type=float, default=0.25)
+    ap.add_argument("--part-bytes", type=float, default=4 * 1024 * 1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-timing", action="store_true", help="skip per-kernel CUDA events")
+    ap.add_argument("--param", action="append", default=[], help="key=value engine parameter")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers --
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(local_units: float, local_ms: float, world: int, group=None):
+    """Whole-job throughput over ranks: sum of units / max of times."""
+    if world == 1:
+        return local_units, local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_units], dtype=torch.float64)
+    m = torch.tensor([local_ms], dtype=torch.float64)
+    if dist.get_backend(group) == "nccl":
+        t, m = t.cuda(), m.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item()), float(m.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_graphs(scale):
+    from gen import graphgen as gg
+    g = gg.rmat(scale, seed=1, wmax=64)
+    s = gg.symmetrize(g)
+    return g, s
+
+
+# ------------------------------------------------------- reference arm ----
+def cpu_oracle_sample(g, budget_s: float = 20.0):
+    """The oracle (plain single-threaded C) on a bounded sample: BFS from 0,
+    then Dijkstra from 0 if the BFS left time in the budget."""
+    from oracle import oracle as orc
+    t0 = time.perf_counter()
+    _, e_bfs = orc.bfs(g, 0)
+    t1 = time.perf_counter()
+    edges, secs, sample = e_bfs, t1 - t0, "oracle BFS from vertex 0 on the full graph"
+    if (t1 - t0) * 6 < budget_s:
+        _, e_sp, _ = orc.sssp(g, 0)
+        t2 = time.perf_counter()
+        edges += e_sp
+        secs = t2 - t0
+        sample += " + oracle Dijkstra from vertex 0 on the full graph"
+    return edges, secs, sample
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    g, _ = make_graphs(args.scale)
+    from oracle import oracle as orc
+    orc.build()
+    total_e, total_s = 0, 0.0
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        lv, e = orc.bfs(g, 0)
+        dt = time.perf_counter() - t0
+        sample = "oracle FIFO BFS from vertex 0 on the full graph, one per step"
+        if i >= args.warmup:
+            total_e += e
+            total_s += dt
+    v = total_e / total_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale} BFS (oracle, CPU, 1 thread)"},
+            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- ours ----
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2208_14935_gb300 import build as bld
+    bld.build()
+    from paper_2208_14935_gb300 import hytg
+    t_gen = time.perf_counter()
+    g, s = make_graphs(args.scale)
+    t_gen = time.perf_counter() - t_gen
+    graph_bytes = g.E * 8 + (g.V + 1) * 8
+    sym_bytes = s.E * 4 + (s.V + 1) * 8
+    params = {"part_bytes": args.part_bytes, "timing": 0 if args.no_timing else 1}
+    for kv in args.param:
+        k, v = kv.split("=")
+        params[k] = float(v)
+    eng = hytg.Engine(g, budget=int(args.budget_frac * graph_bytes), device=local, params=params)
+    eng_s = hytg.Engine(s, budget=int(args.budget_frac * sym_bytes), device=local, params=params)
+    memcpy_gbs, zc_gbs = eng.probe_link(1 << 30, 10)
+
+    def one_step(collect):
+        per = {}
+        for algo in ALGOS:
+            e = eng_s if algo == "cc" else eng
+            src = 0 if algo in ("bfs", "sssp") else None
+            t0 = time.perf_counter()
+            hytg.hytg_run(e.ctx, hytg.ALGOS[algo], None if src is None else [src])
+            out = hytg.hytg_fetch_result(e.ctx, e.V, hytg.ALGOS[algo])
+            wall = (time.perf_counter() - t0) * 1e3
+            st = e.stats()
+            per[algo] = {"stats": st, "wall_ms": wall, "d2h": out.nbytes,
+                         "h2d": 0 if src is None else 4}
+        return per
+
+    for _ in range(args.warmup):
+        one_step(False)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    steps = []
+    for _ in range(args.steps):
+        steps.append(one_step(True))
+    barrier(world)
+    clk = clocks.stop()
+
+    edges = sum(p[a]["stats"]["edges_relaxed"] for p in steps for a in ALGOS)
+    dev_ms = sum(p[a]["stats"]["device_ms"] for p in steps for a in ALGOS)
+    wall_ms = sum(p[a]["wall_ms"] for p in steps for a in ALGOS)
+    launches = sum(p[a]["stats"]["kernel_launches"] for p in steps for a in ALGOS)
+    tot_edges, max_ms = aggregate(float(edges), dev_ms, world)
+    tot_edges_w, max_wall = aggregate(float(edges), wall_ms, world)
+    value = tot_edges / (max_ms * 1e-3) / 1e9
+    e2e = tot_edges_w / (max_wall * 1e-3) / 1e9
+
+    # host link: bytes moved over the link by the F, C and Z routes / device time
+    link_bytes = sum(sum(p[a]["stats"]["link_bytes"]) for p in steps for a in ALGOS)
+    link_gbs = link_bytes / (dev_ms * 1e-3) / 1e9
+    per_algo = {}
+    for a in ALGOS:
+        ed = sum(p[a]["stats"]["edges_relaxed"] for p in steps)
+        ms = sum(p[a]["stats"]["device_ms"] for p in steps)
+        st = steps[-1][a]["stats"]
+        per_algo[a] = {"gteps": ed / (ms * 1e-3) / 1e9, "ms": ms / len(steps),
+                       "iterations": st["iterations"], "edges_relaxed": st["edges_relaxed"],
+                       "route_partitions": dict(zip(hytg.ROUTE_NAMES, st["route_partitions"])),
+                       "route_edges": dict(zip(hytg.ROUTE_NAMES, st["route_edges"])),
+                       "link_bytes": sum(st["link_bytes"])}
+
+    # dominant kernel kind over the timed steps (per-kind CUDA events)
+    kinds = hytg.KERNEL_KINDS
+    kms = [0.0] * 12
+    kcnt = [0] * 12
+    for p in steps:
+        for a in ALGOS:
+            for i in range(12):
+                kms[i] += p[a]["stats"]["kernel_ms"][i]
+                kcnt[i] += p[a]["stats"]["kernel_count"][i]
+    peaks, peak_src = measured_peaks()
+    roofline = None
+    if not args.no_timing:
+        relax = {"relax_Z": 7, "relax_cache": 3, "relax_F": 4, "relax_C": 6, "gather_C": 5}
+        dom = max(relax, key=lambda k: kms[relax[k]])
+        route_of = {"relax_Z": 4, "relax_cache": 1, "relax_F": 2, "relax_C": 3, "gather_C": 3}
+        r = route_of[dom]
+        alg_bytes = 0
+        for p in steps:
+            for a in ALGOS:
+                d1 = 8 if a == "sssp" else 4
+                alg_bytes += p[a]["stats"]["route_edges"][r] * d1
+        ms = kms[relax[dom]]
+        achieved = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        if dom in ("relax_Z", "gather_C"):
+            roofline = {"kernel": dom, "bound": "host_link", "achieved": achieved, "peak": memcpy_gbs,
+                        "unit": "GB/s", "frac": achieved / memcpy_gbs if memcpy_gbs else None,
+                        "traffic": None, "peak_source": "pinned cudaMemcpyAsync H2D probe, same run",
+                        "launches": kcnt[relax[dom]], "ms_total": ms}
+        else:
+            hbm = float(peaks.get("hbm_gbs", 6800.0))
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                        "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                        "launches": kcnt[relax[dom]], "ms_total": ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        e_cpu, s_cpu, sample = cpu_oracle_sample(g)
+        cpu = {"value": e_cpu / s_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": sample, "seconds": s_cpu, "host_cores": os.cpu_count()}
+
+    h2d = sum(p[a]["h2d"] for p in steps for a in ALGOS) // len(steps)
+    d2h = sum(p[a]["d2h"] for p in steps for a in ALGOS) // len(steps)
+    link_per_step = link_bytes // len(steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 (PageRank f32)", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale} bfs+sssp+cc+pagerank, edges in pinned host memory, "
+                               f"budget {args.budget_frac:.0%} of graph bytes",
+                   "V": g.V, "E": g.E, "E_sym": s.E, "budget_bytes": int(args.budget_frac * graph_bytes),
+                   "budget_bytes_cc": int(args.budget_frac * sym_bytes),
+                   "part_bytes": args.part_bytes, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (edge arrays in host memory, 2 GiB + 2 GiB)",
+                   "graph_gen_s": round(t_gen, 1)},
+        "host_link": {"achieved_gbs": link_gbs, "memcpy_probe_gbs": memcpy_gbs,
+                      "zerocopy_probe_gbs": zc_gbs, "frac_of_measured": link_gbs / memcpy_gbs,
+                      "bytes_per_step": link_per_step},
+        "batched_vs_plain": None,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d + link_per_step,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "per_algo": per_algo,
+        "kernel_ms": {kinds[i]: kms[i] for i in range(12) if kcnt[i]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    eng.close()
+    eng_s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

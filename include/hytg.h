@@ -1,0 +1,213 @@
+/*
+ * hytg -- hybrid host-to-GPU transfer graph engine for one GB300 (sm_103a).
+ *
+ * The engine runs vertex-centric push algorithms (BFS, SSSP, connected
+ * components, delta-PageRank) over a CSR graph whose edge arrays live in
+ * pinned host memory, because they exceed a capped device budget.  Vertex
+ * data (row offsets, values, frontier) stays on the GPU and edge data in host
+ * memory, as stated in the paper's problem setting (Sec. I; Sec. II-A, last
+ * paragraph; Sec. IV).  Each iteration, a per-partition cost model (Sec. V-A,
+ * Eq. 1-3) picks one of four routes for each partition's active edges:
+ *   CACHE  the partition is resident in a device region carved from the budget;
+ *   F      explicit copy of the whole partition (ExpTM-filter, Eq. 1);
+ *   C      GPU compaction of only the active adjacency lists (ExpTM-compaction,
+ *          Eq. 2), gathered from mapped host memory into a device buffer;
+ *   Z      zero-copy: the relax kernel reads mapped host memory (ImpTM-ZC, Eq. 3);
+ * partitions are then combined into tasks (Sec. V-B, Alg. 1) and relaxed by
+ * push kernels on several streams (Sec. VI-B).
+ *
+ * Conventions for every call:
+ *   - every function returns an hytg_status; no exception crosses the ABI;
+ *   - host pointers are plain host memory owned by the caller and are only
+ *     read (inputs) or written (outputs) during the call;
+ *   - after any error other than HYTG_ERR_CUDA the context stays usable;
+ *     after HYTG_ERR_CUDA only hytg_destroy is meaningful;
+ *   - one context is driven by one host thread at a time;
+ *   - hytg_last_error() returns a message for the last failed call.
+ */
+#ifndef HYTG_H
+#define HYTG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hytg_ctx hytg_ctx;
+
+typedef enum {
+    HYTG_OK = 0,
+    HYTG_ERR_ARG = 1,       /* invalid argument (bad CSR, source out of range, bad key) */
+    HYTG_ERR_CUDA = 2,      /* a CUDA call failed; the context is no longer usable */
+    HYTG_ERR_BUDGET = 3,    /* device budget below one staging slot plus compaction buffer */
+    HYTG_ERR_HOSTMEM = 4,   /* pinned host allocation failed */
+    HYTG_ERR_OVERFLOW = 5,  /* an SSSP distance reached 0xFFFFFFFE (does not fit 32 bits) */
+    HYTG_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out */
+    HYTG_ERR_STATE = 7      /* call out of order (no graph loaded, no completed run) */
+} hytg_status;
+
+typedef enum {
+    HYTG_BFS = 0,       /* level[v]: hops from the source (Sec. VII-A)            */
+    HYTG_SSSP = 1,      /* dist[v]: min sum of uint32 weights (Sec. II-A, Fig. 1)  */
+    HYTG_CC = 2,        /* label[v]: min vertex id of v's component; needs a symmetric CSR */
+    HYTG_PAGERANK = 3,  /* delta-based PageRank (Sec. VI-A), ranks normalised to sum 1 */
+    HYTG_PPR = 4        /* personalised PageRank from one seed, normalised to sum 1 */
+} hytg_algo;
+
+typedef enum {
+    HYTG_ROUTE_NONE = 0,   /* partition has no active out-edge this iteration */
+    HYTG_ROUTE_CACHE = 1,
+    HYTG_ROUTE_F = 2,
+    HYTG_ROUTE_C = 3,
+    HYTG_ROUTE_Z = 4
+} hytg_route;
+
+#define HYTG_UNREACHED 0xFFFFFFFFu
+
+/* Totals of the last hytg_run.  Index [r] of the per-route arrays is a
+ * hytg_route value. */
+typedef struct hytg_stats {
+    uint32_t iterations;
+    uint32_t status;                  /* hytg_status of the run */
+    uint64_t edges_relaxed;           /* sum over iterations of active out-edges (TEPS numerator) */
+    uint64_t vertices_processed;      /* sum over iterations of active vertices */
+    uint64_t route_partitions[5];     /* partition-iterations per route */
+    uint64_t route_vertices[5];       /* active vertices (degree > 0) per route */
+    uint64_t route_edges[5];          /* active edges per route */
+    uint64_t link_bytes[5];           /* host-link bytes per route: F whole partitions,
+                                         C and Z 128-byte lines spanned, cache 0 */
+    uint64_t cache_fill_bytes;        /* bytes copied to fill the resident cache this run */
+    uint64_t f_tasks;                 /* F copy tasks after combination (Sec. V-B) */
+    uint64_t kernel_launches;         /* kernels launched by the run */
+    double wall_ms;                   /* host wall time of hytg_run */
+    double kernel_ms[12];             /* device time per kernel kind (CUDA events), when
+                                         the "timing" parameter is 1; see HYTG_K_* */
+    uint64_t kernel_count[12];        /* launches per kernel kind (timing on) */
+    double pr_residual_sum;           /* PageRank/PPR: sum of |delta| left at convergence */
+    double pr_rank_sum;               /* PageRank/PPR: sum of raw ranks */
+    double device_ms;                 /* CUDA-event time of the run on its main stream, which
+                                         joins every other stream of the run */
+} hytg_stats;
+
+/* kernel kinds indexing kernel_ms / kernel_count */
+enum {
+    HYTG_K_INIT = 0, HYTG_K_COUNT = 1, HYTG_K_BIN = 2, HYTG_K_RELAX_CACHE = 3,
+    HYTG_K_RELAX_F = 4, HYTG_K_GATHER_C = 5, HYTG_K_RELAX_C = 6, HYTG_K_RELAX_Z = 7,
+    HYTG_K_COPY_F = 8, HYTG_K_FINAL = 9, HYTG_K_CACHE_FILL = 10, HYTG_K_OTHER = 11
+};
+
+/* Sizes and placement after load / budget / the last plan. */
+typedef struct hytg_info {
+    uint64_t V, E;
+    uint32_t weighted;
+    uint32_t n_parts;                 /* partitions of the edge arrays (Sec. IV) */
+    uint64_t part_edges;              /* target edges per partition */
+    uint64_t slot_edges;              /* edges per staging slot (k partitions) */
+    uint32_t n_slots;                 /* staging slots = F streams in use */
+    uint32_t n_cached;                /* partitions [0, n_cached) resident for the last algo */
+    uint64_t budget_bytes;            /* device budget for edge-side data */
+    uint64_t budget_used_bytes;       /* cache + staging + compaction buffer */
+    uint64_t compact_edges;           /* capacity of the compaction buffer, in edges */
+    uint64_t vertex_state_bytes;      /* device bytes held for vertex-side data */
+    uint64_t pinned_host_bytes;       /* pinned host bytes held for edge arrays */
+} hytg_info;
+
+/* Create a context on CUDA device `device`.  *out receives an owned handle. */
+hytg_status hytg_create(hytg_ctx **out, int device);
+
+/* Release every device and pinned host allocation of the context. */
+hytg_status hytg_destroy(hytg_ctx *ctx);
+
+/* Load a CSR graph (Sec. IV: the neighbour index stays on the GPU, the
+ * neighbour and weight arrays in host memory).  offsets: V+1 uint64, with
+ * offsets[0] = 0, offsets[V] = E, non-decreasing; dst: E uint32, each < V;
+ * weights: E uint32 or NULL for an unweighted graph.  The arrays are copied
+ * into library-owned pinned, device-mapped host memory; the caller keeps
+ * ownership of its arrays.  V must be in [1, 2^32 - 1].  Replaces any earlier
+ * graph.  Errors: HYTG_ERR_ARG (bad CSR), HYTG_ERR_HOSTMEM, HYTG_ERR_CUDA. */
+hytg_status hytg_load_csr(hytg_ctx *ctx, uint64_t V, uint64_t E, const uint64_t *offsets,
+                          const uint32_t *dst, const uint32_t *weights);
+
+/* Hard cap on device bytes for edge-side data: resident cache, staging slots
+ * for explicit copies and the compaction buffer.  Vertex-side data is not
+ * counted (it is reported by hytg_get_info).  A budget that cannot hold one
+ * staging slot of the largest partition plus one partition's worth of
+ * compaction buffer returns HYTG_ERR_BUDGET. */
+hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
+
+/* Set a tunable.  Keys: "alpha", "beta", "gamma" (Sec. V-A selection and
+ * RTT_zc, stored as multiples of 1e-6), "m" (request bytes), "MR" (outstanding
+ * requests), "k" (partitions per F task, Sec. V-B), "part_bytes" (partition
+ * size in bytes of 4-byte entries, Sec. V-B), "streams" (F streams/slots),
+ * "staging_frac", "compact_frac" (shares of the budget), "force_route"
+ * (-1 cost model, 1 cache, 2 F, 3 C, 4 Z, 5 random per partition per
+ * iteration), "seed" (for force_route 5), "pr_damping", "pr_eps" (FP32
+ * residual threshold), "max_iters", "timing" (1: CUDA-event time per kernel
+ * kind).  Changing "part_bytes" re-partitions the loaded graph.
+ * Unknown key or value out of range: HYTG_ERR_ARG. */
+hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);
+hytg_status hytg_get_param(hytg_ctx *ctx, const char *key, double *value);
+
+/* Run `algo` to convergence (Sec. IV: cost-aware task generation and task
+ * scheduling alternate until no vertex is active).  sources: n_sources
+ * vertex ids (host memory); BFS/SSSP/PPR take exactly one, CC/PAGERANK
+ * ignore them (pass NULL, 0).  The result stays on the device until
+ * hytg_fetch_result.  Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no
+ * budget), HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_CUDA. */
+hytg_status hytg_run(hytg_ctx *ctx, hytg_algo algo, const uint32_t *sources, uint32_t n_sources);
+
+/* Copy the last run's result into caller-owned host memory `out` of
+ * out_bytes >= 4*V bytes: uint32 per vertex (BFS level, SSSP distance, CC
+ * label; HYTG_UNREACHED when unreached) or float per vertex (PageRank/PPR,
+ * normalised to sum 1).  HYTG_ERR_STATE if no run completed. */
+hytg_status hytg_fetch_result(hytg_ctx *ctx, void *out, uint64_t out_bytes);
+
+/* Raw delta-PageRank state of the last PageRank/PPR run: rank and the
+ * residual delta per vertex (float, V entries each; either may be NULL). */
+hytg_status hytg_fetch_pagerank_state(hytg_ctx *ctx, float *rank, float *delta, uint64_t V);
+
+hytg_status hytg_get_stats(hytg_ctx *ctx, hytg_stats *out);
+hytg_status hytg_get_info(hytg_ctx *ctx, hytg_info *out);
+
+/* Partition table (Sec. IV): vertex bounds, n_parts + 1 uint64 entries.
+ * Partitions start on multiples of 32 vertices; each is the longest run with
+ * at most part_edges edges, or a single 32-vertex run if that run alone has
+ * more.  cap: entries available in vbounds. */
+hytg_status hytg_get_partitions(hytg_ctx *ctx, uint64_t *vbounds, uint32_t cap, uint32_t *n_parts);
+
+/* Cost analysis and engine selection alone (Sec. V-A, Alg. 1 cost part) for
+ * a caller-given frontier: active (V bytes, nonzero = active) is uploaded,
+ * the count and selection kernels run on the device, and the per-partition
+ * results come back: routes[n_parts] (hytg_route), and, if non-NULL,
+ * counts[3 * n_parts] = {|A_i|, active edges, 128-byte lines} per partition.
+ * The resident set is the cache plan for `algo` under the current budget. */
+hytg_status hytg_plan(hytg_ctx *ctx, hytg_algo algo, const uint8_t *active, uint8_t *routes,
+                      uint64_t *counts, uint32_t cap);
+
+/* Host-link probe (the measured denominators of the link roofline): pinned
+ * host-to-device cudaMemcpyAsync bandwidth over `bytes`, best of `reps`, and
+ * a zero-copy kernel reading the same pinned buffer in 128-byte lines.
+ * Results in GB/s (1e9 bytes/s). */
+hytg_status hytg_probe_link(hytg_ctx *ctx, uint64_t bytes, uint32_t reps, double *memcpy_gbs,
+                            double *zerocopy_gbs);
+
+/* Per-iteration record of the last run (up to cap records). */
+typedef struct hytg_iter_record {
+    uint64_t active_vertices;
+    uint64_t active_edges;
+    uint32_t route_partitions[5];
+    uint32_t f_tasks;
+    uint64_t route_edges[5];
+    uint64_t link_bytes;
+} hytg_iter_record;
+hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t cap, uint32_t *n);
+
+const char *hytg_status_str(hytg_status s);
+const char *hytg_last_error(hytg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYTG_H */

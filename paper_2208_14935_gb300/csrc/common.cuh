@@ -1,0 +1,174 @@
+// Internal declarations shared by the kernels and the host runtime of the
+// hybrid-transfer graph engine.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hytg {
+
+constexpr int kRoutes = 5;            // NONE, CACHE, F, C, Z (hytg_route)
+constexpr int kRouteNone = 0, kRouteCache = 1, kRouteF = 2, kRouteC = 3, kRouteZ = 4;
+
+// Frontier bitmap: one bit per vertex, 32-bit words; kernels walk it in
+// segments of 128 words (4096 vertices), one warp per segment.
+constexpr int kSegWords = 128;
+constexpr int kSegVerts = kSegWords * 32;
+
+// Edge tiles of the load-balanced relax kernels.
+constexpr int kRelaxBlock = 256;
+constexpr int kRelaxIPT = 8;
+constexpr int kTile = kRelaxBlock * kRelaxIPT;   // 2048 edges per tile
+
+constexpr int kSelectBlock = 1024;
+
+enum Algo : int { kBFS = 0, kSSSP = 1, kCC = 2, kPR = 3, kPPR = 4 };
+
+// Cost-model parameters of one iteration (Sec. V-A).  alpha, beta, gamma are
+// rationals num / 1e6 so that the device decision is exact.
+struct CostParams {
+    unsigned long long alpha_num, beta_num, gamma_num;   // over kParamDen
+    unsigned long long m, MR;
+    unsigned long long d1;          // bytes read per edge (4 or 8)
+    unsigned long long d2;          // bytes per index entry (8)
+    unsigned int n_cached;          // partitions [0, n_cached) are resident
+    int force_route;                // -1 cost model; 1..4 forced route; 5 random
+    unsigned long long seed;        // for force_route 5
+    unsigned int iteration;
+};
+constexpr unsigned long long kParamDen = 1000000ull;
+
+// Device-side summary of one iteration, copied to the host in one piece
+// together with the per-partition arrays that follow it in memory.
+struct alignas(16) Summary {
+    unsigned long long n_active;                 // active vertices (any degree)
+    unsigned long long route_entries[kRoutes];   // list entries (active, degree > 0)
+    unsigned long long route_edges[kRoutes];     // active edges
+    unsigned long long route_lines[kRoutes];     // 128-byte lines (cost-model count)
+    unsigned long long route_entry_base[kRoutes];// first index of each route in the list
+    unsigned long long route_tile_base[kRoutes]; // first tile of each route
+    unsigned int route_parts[kRoutes];
+    unsigned int overflow;                       // SSSP distance overflow seen
+};
+
+// Per-partition arrays, laid out right after the Summary in one buffer.
+struct PartArrays {
+    unsigned long long *n_act;      // |A_i|
+    unsigned long long *entries;    // active vertices with degree > 0
+    unsigned long long *edges;      // sum of D_o over A_i
+    unsigned long long *lines;      // 128-byte lines spanned (all arrays read)
+    unsigned long long *route_entry;// first list index of the partition inside its route
+    unsigned long long *route_edge; // first edge index of the partition inside its route
+    unsigned long long *entry_delta;// list index = global entry prefix + entry_delta
+    unsigned long long *edge_delta; // route edge index = global edge prefix + edge_delta
+    unsigned char *route;           // hytg_route
+};
+
+// The list of active vertices of one iteration, grouped by route and, inside
+// a route, ordered by partition and vertex id.
+struct ListArrays {
+    unsigned long long *ebase;      // first edge of the entry in its route's edge space
+    unsigned long long *soff;       // row offset of the vertex (its first edge in the CSR)
+    unsigned int *pay;              // value pushed along its edges (uint32 or float bits)
+    unsigned int *tile_first;       // per route tile: list entry (route-relative) holding its first edge
+    unsigned long long cap_entries; // capacity of ebase / soff / pay
+    unsigned long long cap_tiles;   // capacity of tile_first
+    unsigned int *err;              // device word: nonzero if an index check failed
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ unsigned long long lines_spanned(unsigned long long start,
+                                                            unsigned long long len,
+                                                            unsigned long long m) {
+    return len == 0 ? 0ull : (start + len - 1) / m - start / m + 1;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// inclusive warp scan
+__device__ __forceinline__ unsigned long long warp_scan_u64(unsigned long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Counter-based mix used only for the "random route" test mode.
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// ------------------------------------------------------------- launchers
+struct GraphDev {
+    const unsigned long long *off;      // V+1 row offsets (device)
+    unsigned long long V, n_words, n_segs;
+    const unsigned int *part_wb;        // partition bounds in bitmap words, N+1
+    const unsigned long long *part_eb;  // partition bounds in edges, N+1
+    unsigned int N;
+};
+
+struct SegArrays {
+    unsigned long long *entries, *edges;           // per segment totals (pass 1)
+    unsigned long long *entry_prefix, *edge_prefix;// exclusive prefixes (select)
+};
+
+struct AlgoState {
+    int algo;
+    unsigned int *val;       // BFS level / SSSP dist / CC label
+    float *rank, *delta;     // PageRank state
+    float damping, eps;
+    unsigned int *bm_cur, *bm_next;
+    unsigned int *overflow;  // device flag
+    unsigned int n_arrays;   // edge arrays read per edge (1 or 2)
+};
+
+cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
+                         const SegArrays &sa, unsigned long long m, cudaStream_t s);
+cudaError_t launch_select(const GraphDev &g, const PartArrays &pa, const SegArrays &sa,
+                          const CostParams &cp, Summary *sum, cudaStream_t s);
+cudaError_t launch_bin(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
+                       const SegArrays &sa, const ListArrays &la, const Summary *sum,
+                       cudaStream_t s);
+
+// Edge source of a relax / gather launch.
+enum EdgeMode : int { kModeHost = 0, kModeDevice = 1, kModeCompact = 2 };
+
+struct RelaxTask {
+    int route;                          // which route's list / tiles
+    int mode;                           // EdgeMode
+    const unsigned int *dst;            // edge destinations (device or mapped host)
+    const unsigned int *w;              // weights or nullptr
+    long long shift;                    // edge index of dst[0] (device copies)
+    unsigned long long k_begin, k_end;  // edge range in the route's edge space
+    unsigned long long first_entry;     // route-relative entry holding k_begin
+    bool device_sized;                  // take k_end from the summary (k_begin = 0)
+    unsigned long long src_len;         // valid indices of dst / w: [0, src_len)
+};
+
+cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
+                         const RelaxTask &t, int grid_cap, cudaStream_t s);
+cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
+                          unsigned int *out_dst, unsigned int *out_w, int grid_cap,
+                          cudaStream_t s);
+
+cudaError_t launch_init(const AlgoState &st, unsigned long long V, unsigned long long n_words_alloc,
+                        unsigned int source, cudaStream_t s);
+cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float *out,
+                               double *sums, cudaStream_t s);
+cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *bm,
+                                 unsigned long long V, unsigned long long n_words_alloc,
+                                 cudaStream_t s);
+cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
+                            int grid, cudaStream_t s);
+
+}  // namespace hytg

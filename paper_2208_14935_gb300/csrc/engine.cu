@@ -1,0 +1,1091 @@
+// Host runtime and C ABI of the hybrid-transfer graph engine.
+//
+// One hytg_run alternates, until no vertex is active (Sec. IV, overview):
+//   1. cost-aware task generation on the device (Sec. V-A): k_count,
+//      k_select, then one small device-to-host copy of the per-partition
+//      routes and counts (Alg. 1, "copy ... to host");
+//   2. k_bin builds the per-route active lists; the cache and zero-copy
+//      routes are launched at once with device-side sizes;
+//   3. on the host, task combination (Sec. V-B, Alg. 1 combination part):
+//      up to k consecutive F partitions become one copy plus one relax; the
+//      C partitions are compacted and relaxed in chunks of the compaction
+//      buffer;
+//   4. multi-stream issue (Sec. VI-B): every F task on its own stream and
+//      staging slot (copy engine overlapped with the relax of the previous
+//      task), the C route on another stream, cache and Z on the main stream.
+// The next iteration's planning kernels wait, on the device, for every
+// stream of the previous one, so the host only blocks on the summary copy.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <functional>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "hytg.h"
+
+using namespace hytg;
+
+namespace {
+
+constexpr int kMaxStreams = 8;
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct Carve {
+    int n_arrays = 0;           // 0: not planned
+    uint64_t budget = 0, part_edges = 0;
+    uint64_t slot_edges = 0;
+    uint32_t n_slots = 0;
+    uint64_t compact_edges = 0;
+    uint32_t n_cached = 0;
+    uint64_t cache_edges = 0;
+    uint32_t *cache_dst = nullptr, *cache_w = nullptr;
+    uint32_t *slot_dst[kMaxStreams] = {}, *slot_w[kMaxStreams] = {};
+    uint32_t *cmp_dst = nullptr, *cmp_w = nullptr;
+    uint64_t used = 0;
+};
+
+}  // namespace
+
+struct hytg_ctx {
+    int device = 0;
+    std::string err;
+
+    cudaStream_t s_main = nullptr, s_c = nullptr;
+    cudaStream_t s_f[kMaxStreams] = {};
+    cudaEvent_t ev_sum[2] = {}, ev_bin = nullptr, ev_f[kMaxStreams] = {}, ev_c = nullptr;
+    cudaEvent_t ev_run[2] = {};                          // device time of a run
+
+    // graph
+    bool loaded = false;
+    uint64_t V = 0, E = 0;
+    bool weighted = false;
+    uint32_t *h_dst = nullptr, *h_w = nullptr;          // pinned, mapped
+    const uint32_t *m_dst = nullptr, *m_w = nullptr;    // device view of the same memory
+    std::vector<uint64_t> h_off;
+
+    // partitions
+    uint64_t part_edges = 0, max_part_edges = 0;
+    std::vector<uint64_t> part_vb, part_eb;
+    std::vector<uint32_t> part_wb;
+    unsigned int *d_part_wb = nullptr;
+    unsigned long long *d_part_eb = nullptr;
+
+    // vertex-side device state
+    unsigned long long *d_off = nullptr;
+    unsigned int *d_val = nullptr;
+    float *d_delta = nullptr;
+    unsigned int *d_bm[2] = {};
+    unsigned int *d_overflow = nullptr;
+    unsigned int *d_err = nullptr;                       // device index-check flags
+    uint64_t n_tiles_alloc = 0;
+    double *d_prsums = nullptr;
+    float *d_out = nullptr;                              // normalised PageRank
+    unsigned long long n_segs = 0, n_words_alloc = 0;
+    // lists
+    unsigned long long *d_ebase = nullptr, *d_soff = nullptr;
+    unsigned int *d_pay = nullptr, *d_tiles = nullptr;
+    unsigned long long *d_seg = nullptr;                 // 4 arrays of n_segs
+    // summary + per-partition arrays
+    void *d_sumbuf = nullptr;
+    void *h_sumbuf[2] = {};
+    size_t sum_host_bytes = 0, sum_dev_bytes = 0;
+    uint64_t vertex_bytes = 0;
+
+    // budget pool
+    uint64_t budget = 0;
+    void *d_pool = nullptr;
+    Carve carve;
+    int cache_filled_arrays = 0;
+    uint32_t cache_filled_n = 0;
+
+    // parameters
+    double alpha = 0.8, beta = 0.4, gamma = 0.625, m = 128, MR = 256, k = 4;
+    double part_bytes = 4.0 * 1024 * 1024;
+    double streams = 4, staging_frac = 0.5, compact_frac = 0.25;
+    double force_route = -1, seed = 1, pr_damping = 0.85, pr_eps = 1e-9, max_iters = 1e8;
+    double timing = 0;
+
+    // last run
+    bool have_result = false;
+    int last_algo = -1;
+    hytg_stats stats{};
+    std::vector<hytg_iter_record> iters;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+const char *kStatusStr[] = {"ok", "invalid argument", "CUDA error", "device budget too small",
+                            "pinned host allocation failed", "SSSP distance overflow",
+                            "device wait timed out", "call out of order"};
+
+hytg_status fail(hytg_ctx *c, hytg_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return fail(c, HYTG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_graph(hytg_ctx *c) {
+    if (c->h_dst) cudaFreeHost(c->h_dst);
+    if (c->h_w) cudaFreeHost(c->h_w);
+    c->h_dst = c->h_w = nullptr;
+    c->m_dst = c->m_w = nullptr;
+    dfree(c->d_off); dfree(c->d_val); dfree(c->d_delta); dfree(c->d_bm[0]); dfree(c->d_bm[1]);
+    dfree(c->d_out); dfree(c->d_ebase); dfree(c->d_soff); dfree(c->d_pay); dfree(c->d_tiles);
+    dfree(c->d_seg); dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf);
+    for (int i = 0; i < 2; ++i) {
+        if (c->h_sumbuf[i]) cudaFreeHost(c->h_sumbuf[i]);
+        c->h_sumbuf[i] = nullptr;
+    }
+    c->loaded = false;
+    c->have_result = false;
+    c->h_off.clear();
+    c->cache_filled_arrays = 0;
+    c->cache_filled_n = 0;
+    c->carve = Carve();
+}
+
+void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &fn) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < (1u << 20)) nt = 1;
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+    fn(0, n / nt);
+    for (auto &x : th) x.join();
+}
+
+// Layout of the summary buffer: Summary, then per-partition arrays; the
+// prefix up to `route` is copied to the host each iteration.
+struct SumLayout {
+    size_t n_act, entries, edges, lines, route_entry, route_edge, route, host_end, entry_delta,
+        edge_delta, total;
+};
+SumLayout sum_layout(uint32_t N) {
+    SumLayout L;
+    size_t o = (sizeof(Summary) + 15) & ~size_t(15);
+    const size_t a = (size_t)N * 8;
+    L.n_act = o; o += a;
+    L.entries = o; o += a;
+    L.edges = o; o += a;
+    L.lines = o; o += a;
+    L.route_entry = o; o += a;
+    L.route_edge = o; o += a;
+    L.route = o; o += ((size_t)N + 15) & ~size_t(15);
+    L.host_end = o;
+    L.entry_delta = o; o += a;
+    L.edge_delta = o; o += a;
+    L.total = o;
+    return L;
+}
+
+PartArrays part_arrays(hytg_ctx *c) {
+    SumLayout L = sum_layout((uint32_t)(c->part_vb.size() - 1));
+    char *b = (char *)c->d_sumbuf;
+    PartArrays pa;
+    pa.n_act = (unsigned long long *)(b + L.n_act);
+    pa.entries = (unsigned long long *)(b + L.entries);
+    pa.edges = (unsigned long long *)(b + L.edges);
+    pa.lines = (unsigned long long *)(b + L.lines);
+    pa.route_entry = (unsigned long long *)(b + L.route_entry);
+    pa.route_edge = (unsigned long long *)(b + L.route_edge);
+    pa.route = (unsigned char *)(b + L.route);
+    pa.entry_delta = (unsigned long long *)(b + L.entry_delta);
+    pa.edge_delta = (unsigned long long *)(b + L.edge_delta);
+    return pa;
+}
+
+// Partition rule (Sec. IV edge-balanced chunk partitioning, read with word-
+// aligned bounds): starting at b, the partition ends at the largest multiple
+// of 32 vertices e (or V) with off[e] - off[b] <= part_edges; if even the
+// first 32 vertices hold more, it is those 32 alone.
+void make_partitions(hytg_ctx *c) {
+    const uint64_t V = c->V, pe = c->part_edges;
+    const std::vector<uint64_t> &off = c->h_off;
+    c->part_vb.assign(1, 0);
+    uint64_t b = 0;
+    while (b < V) {
+        // binary search over aligned ends b + 32 j (and V)
+        uint64_t lo = 0, hi = (V - b + 31) / 32;     // j in [1, hi] candidate; find largest ok
+        auto end_of = [&](uint64_t j) { return std::min(V, b + 32 * j); };
+        while (lo < hi) {
+            uint64_t mid = (lo + hi + 1) / 2;
+            if (off[end_of(mid)] - off[b] <= pe) lo = mid; else hi = mid - 1;
+        }
+        uint64_t e = lo == 0 ? end_of(1) : end_of(lo);
+        c->part_vb.push_back(e);
+        b = e;
+    }
+    if (V == 0) c->part_vb.push_back(0);
+    const size_t N = c->part_vb.size() - 1;
+    c->part_eb.resize(N + 1);
+    c->part_wb.resize(N + 1);
+    c->max_part_edges = 0;
+    for (size_t i = 0; i <= N; ++i) {
+        c->part_eb[i] = off[c->part_vb[i]];
+        c->part_wb[i] = (uint32_t)((c->part_vb[i] + 31) / 32);
+        if (i) c->max_part_edges = std::max(c->max_part_edges, c->part_eb[i] - c->part_eb[i - 1]);
+    }
+}
+
+hytg_status upload_partitions(hytg_ctx *c) {
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf);
+    for (int i = 0; i < 2; ++i) {
+        if (c->h_sumbuf[i]) cudaFreeHost(c->h_sumbuf[i]);
+        c->h_sumbuf[i] = nullptr;
+    }
+    CK(cudaMalloc(&c->d_part_wb, (N + 1) * sizeof(unsigned int)));
+    CK(cudaMalloc(&c->d_part_eb, (N + 1) * sizeof(unsigned long long)));
+    CK(cudaMemcpy(c->d_part_wb, c->part_wb.data(), (N + 1) * sizeof(unsigned int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_part_eb, c->part_eb.data(), (N + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    SumLayout L = sum_layout(N);
+    c->sum_dev_bytes = L.total;
+    c->sum_host_bytes = L.host_end;
+    CK(cudaMalloc(&c->d_sumbuf, L.total));
+    CK(cudaMemset(c->d_sumbuf, 0, L.total));
+    for (int i = 0; i < 2; ++i) CK(cudaHostAlloc(&c->h_sumbuf[i], L.host_end, cudaHostAllocDefault));
+    c->carve = Carve();
+    c->cache_filled_arrays = 0;
+    return HYTG_OK;
+}
+
+// Split the budget into staging slots (F), the compaction buffer (C) and the
+// resident cache (the rest, whole partitions from id 0 upwards).
+hytg_status plan_carve(hytg_ctx *c, int n_arrays) {
+    Carve &cv = c->carve;
+    const uint64_t pe = c->part_edges;
+    Carve n;
+    n.n_arrays = n_arrays;
+    n.budget = c->budget;
+    n.part_edges = pe;
+    const uint64_t eb = 4ull * n_arrays;
+    const uint64_t min_slot = std::max<uint64_t>(c->max_part_edges, 1);
+    const uint64_t compact_min = std::max<uint64_t>(kTile, 1);
+    if (c->budget < (min_slot + compact_min) * eb)
+        return fail(c, HYTG_ERR_BUDGET, "device budget " + std::to_string(c->budget) +
+                                            " B is below one staging slot of the largest partition (" +
+                                            std::to_string(min_slot * eb) + " B) plus the minimum compaction buffer (" +
+                                            std::to_string(compact_min * eb) + " B)");
+    uint64_t stage_cap = std::max<uint64_t>((uint64_t)(c->budget * c->staging_frac), min_slot * eb);
+    stage_cap = std::min<uint64_t>(stage_cap, c->budget - compact_min * eb);
+    uint64_t slot_edges = std::max<uint64_t>((uint64_t)c->k * pe, min_slot);
+    if (slot_edges * eb > stage_cap) slot_edges = std::max<uint64_t>(min_slot, stage_cap / eb);
+    uint64_t n_slots = stage_cap / (slot_edges * eb);
+    n_slots = std::max<uint64_t>(1, std::min<uint64_t>(n_slots, (uint64_t)c->streams));
+    uint64_t rem = c->budget - n_slots * slot_edges * eb;
+    uint64_t compact_edges = std::max<uint64_t>(compact_min, (uint64_t)(c->budget * c->compact_frac) / eb);
+    compact_edges = std::min<uint64_t>(compact_edges, rem / eb);
+    compact_edges = compact_edges / kTile * kTile;
+    if (compact_edges < (uint64_t)kTile) compact_edges = kTile;
+    rem -= compact_edges * eb;
+    // cache: largest prefix of whole partitions that fits
+    uint32_t n_cached = 0;
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    while (n_cached < N && c->part_eb[n_cached + 1] * eb <= rem) ++n_cached;
+    n.slot_edges = slot_edges;
+    n.n_slots = (uint32_t)n_slots;
+    n.compact_edges = compact_edges;
+    n.n_cached = n_cached;
+    n.cache_edges = c->part_eb[n_cached];
+    // addresses inside the pool (256-byte aligned pieces)
+    auto align = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+    char *base = (char *)c->d_pool;
+    uint64_t o = 0;
+    n.cache_dst = (uint32_t *)(base + o); o = align(o + n.cache_edges * 4);
+    if (n_arrays == 2) { n.cache_w = (uint32_t *)(base + o); o = align(o + n.cache_edges * 4); }
+    for (uint32_t s = 0; s < n.n_slots; ++s) {
+        n.slot_dst[s] = (uint32_t *)(base + o); o = align(o + slot_edges * 4);
+        if (n_arrays == 2) { n.slot_w[s] = (uint32_t *)(base + o); o = align(o + slot_edges * 4); }
+    }
+    n.cmp_dst = (uint32_t *)(base + o); o = align(o + compact_edges * 4);
+    if (n_arrays == 2) { n.cmp_w = (uint32_t *)(base + o); o = align(o + compact_edges * 4); }
+    // at most 20 pieces, each padded by < 256 B: the pool holds budget + 8 KiB
+    if (o > c->budget + 8192)
+        return fail(c, HYTG_ERR_BUDGET, "internal: budget carve exceeds the pool");
+    n.used = n.cache_edges * eb + n.n_slots * slot_edges * eb + compact_edges * eb;
+    if (c->cache_filled_arrays != n_arrays || c->carve.cache_dst != n.cache_dst ||
+        c->cache_filled_n != n.n_cached)
+        c->cache_filled_arrays = 0;   // cache must be refilled
+    cv = n;
+    return HYTG_OK;
+}
+
+cudaEvent_t pool_event(hytg_ctx *c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+struct ScopedTime {
+    hytg_ctx *c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+        c->stats.kernel_launches += (kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
+        if (c->timing != 0) {
+            a = pool_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ScopedTime() {
+        if (a) {
+            cudaEvent_t b = pool_event(c);
+            cudaEventRecord(b, s);
+            c->timed.push_back({kind, a, b});
+        }
+    }
+};
+
+GraphDev graph_dev(hytg_ctx *c) {
+    GraphDev g;
+    g.off = c->d_off;
+    g.V = c->V;
+    g.n_words = (c->V + 31) / 32;
+    g.n_segs = c->n_segs;
+    g.part_wb = c->d_part_wb;
+    g.part_eb = c->d_part_eb;
+    g.N = (unsigned int)(c->part_vb.size() - 1);
+    return g;
+}
+
+SegArrays seg_arrays(hytg_ctx *c) {
+    SegArrays s;
+    s.entries = c->d_seg;
+    s.edges = c->d_seg + c->n_segs;
+    s.entry_prefix = c->d_seg + 2 * c->n_segs;
+    s.edge_prefix = c->d_seg + 3 * c->n_segs;
+    return s;
+}
+
+ListArrays list_arrays(hytg_ctx *c) {
+    ListArrays l;
+    l.ebase = c->d_ebase;
+    l.soff = c->d_soff;
+    l.pay = c->d_pay;
+    l.tile_first = c->d_tiles;
+    l.cap_entries = c->V;
+    l.cap_tiles = c->n_tiles_alloc;
+    l.err = c->d_err;
+    return l;
+}
+
+CostParams cost_params(hytg_ctx *c, int algo, uint32_t iteration) {
+    CostParams p;
+    auto q = [](double x) { return (unsigned long long)std::llround(x * (double)kParamDen); };
+    p.alpha_num = q(c->alpha);
+    p.beta_num = q(c->beta);
+    p.gamma_num = q(c->gamma);
+    p.m = (unsigned long long)c->m;
+    p.MR = (unsigned long long)c->MR;
+    p.d1 = (algo == kSSSP) ? 8 : 4;
+    p.d2 = 8;
+    p.n_cached = c->carve.n_cached;
+    p.force_route = (int)c->force_route;
+    p.seed = (unsigned long long)c->seed;
+    p.iteration = iteration;
+    return p;
+}
+
+AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
+    AlgoState st;
+    st.algo = algo;
+    st.val = c->d_val;
+    st.rank = (float *)c->d_val;
+    st.delta = c->d_delta;
+    st.damping = (float)c->pr_damping;
+    st.eps = (float)c->pr_eps;
+    st.bm_cur = c->d_bm[cur];
+    st.bm_next = c->d_bm[cur ^ 1];
+    st.overflow = c->d_overflow;
+    st.n_arrays = (algo == kSSSP) ? 2 : 1;
+    return st;
+}
+
+// Issue planning for one iteration on s_main: counts, selection, summary
+// copy (-> ev_sum[buf]), binning (-> ev_bin), and the device-sized cache and
+// zero-copy relaxes.
+hytg_status issue_plan(hytg_ctx *c, int algo, int cur, uint32_t it, int buf, bool with_work) {
+    GraphDev g = graph_dev(c);
+    AlgoState st = algo_state(c, algo, cur);
+    PartArrays pa = part_arrays(c);
+    SegArrays sa = seg_arrays(c);
+    ListArrays la = list_arrays(c);
+    Summary *sum = (Summary *)c->d_sumbuf;
+    const uint32_t N = g.N;
+    CK(cudaMemsetAsync(pa.n_act, 0, (size_t)N * 8 * 4, c->s_main));
+    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_count(g, st, pa, sa, (unsigned long long)c->m, c->s_main)); }
+    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_select(g, pa, sa, cost_params(c, algo, it), sum, c->s_main)); }
+    CK(cudaMemcpyAsync(c->h_sumbuf[buf], c->d_sumbuf, c->sum_host_bytes, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaEventRecord(c->ev_sum[buf], c->s_main));
+    if (!with_work) return HYTG_OK;
+    { ScopedTime t(c, HYTG_K_BIN, c->s_main); CK(launch_bin(g, st, pa, sa, la, sum, c->s_main)); }
+    CK(cudaEventRecord(c->ev_bin, c->s_main));
+    const int cap = 152 * 4;
+    if (c->carve.n_cached > 0) {
+        RelaxTask t{};
+        t.route = kRouteCache; t.mode = kModeDevice; t.dst = c->carve.cache_dst; t.w = c->carve.cache_w;
+        t.shift = 0; t.device_sized = true; t.src_len = c->carve.cache_edges;
+        ScopedTime tm(c, HYTG_K_RELAX_CACHE, c->s_main);
+        CK(launch_relax(st, la, sum, t, cap, c->s_main));
+    }
+    {
+        RelaxTask t{};
+        t.route = kRouteZ; t.mode = kModeHost; t.dst = c->m_dst; t.w = c->m_w; t.shift = 0;
+        t.device_sized = true; t.src_len = c->E;
+        ScopedTime tm(c, HYTG_K_RELAX_Z, c->s_main);
+        CK(launch_relax(st, la, sum, t, cap, c->s_main));
+    }
+    return HYTG_OK;
+}
+
+
+hytg_status ensure_cache(hytg_ctx *c, int n_arrays) {
+    Carve &cv = c->carve;
+    if (c->cache_filled_arrays == n_arrays && c->cache_filled_n == cv.n_cached) return HYTG_OK;
+    if (cv.cache_edges) {
+        ScopedTime t(c, HYTG_K_CACHE_FILL, c->s_main);
+        CK(cudaMemcpyAsync(cv.cache_dst, c->h_dst, cv.cache_edges * 4, cudaMemcpyHostToDevice, c->s_main));
+        if (n_arrays == 2)
+            CK(cudaMemcpyAsync(cv.cache_w, c->h_w, cv.cache_edges * 4, cudaMemcpyHostToDevice, c->s_main));
+        c->stats.cache_fill_bytes += cv.cache_edges * 4 * n_arrays;
+    }
+    c->cache_filled_arrays = n_arrays;
+    c->cache_filled_n = cv.n_cached;
+    return HYTG_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char *hytg_status_str(hytg_status s) {
+    unsigned i = (unsigned)s;
+    return i < sizeof(kStatusStr) / sizeof(kStatusStr[0]) ? kStatusStr[i] : "unknown status";
+}
+
+const char *hytg_last_error(hytg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+hytg_status hytg_create(hytg_ctx **out, int device) {
+    if (!out) return HYTG_ERR_ARG;
+    *out = nullptr;
+    hytg_ctx *c = new (std::nothrow) hytg_ctx();
+    if (!c) return HYTG_ERR_HOSTMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete c; return HYTG_ERR_CUDA; }
+    hytg_status s = HYTG_OK;
+    auto ck = [&](cudaError_t r) { if (r != cudaSuccess && s == HYTG_OK) s = HYTG_ERR_CUDA; };
+    ck(cudaStreamCreateWithFlags(&c->s_main, cudaStreamNonBlocking));
+    ck(cudaStreamCreateWithFlags(&c->s_c, cudaStreamNonBlocking));
+    for (int i = 0; i < kMaxStreams; ++i) {
+        ck(cudaStreamCreateWithFlags(&c->s_f[i], cudaStreamNonBlocking));
+        ck(cudaEventCreateWithFlags(&c->ev_f[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < 2; ++i) ck(cudaEventCreateWithFlags(&c->ev_sum[i], cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&c->ev_c, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) ck(cudaEventCreate(&c->ev_run[i]));
+    ck(cudaMalloc(&c->d_overflow, sizeof(unsigned int)));
+    ck(cudaMalloc(&c->d_err, sizeof(unsigned int)));
+    ck(cudaMemset(c->d_err, 0, sizeof(unsigned int)));
+    ck(cudaMalloc(&c->d_prsums, 2 * sizeof(double)));
+    if (s != HYTG_OK) { hytg_destroy(c); return s; }
+    *out = c;
+    return HYTG_OK;
+}
+
+hytg_status hytg_destroy(hytg_ctx *c) {
+    if (!c) return HYTG_ERR_ARG;
+    cudaSetDevice(c->device);
+    if (c->s_main) cudaStreamSynchronize(c->s_main);
+    free_graph(c);
+    dfree(c->d_pool);
+    dfree(c->d_overflow);
+    dfree(c->d_err);
+    dfree(c->d_prsums);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (int i = 0; i < kMaxStreams; ++i) {
+        if (c->s_f[i]) cudaStreamDestroy(c->s_f[i]);
+        if (c->ev_f[i]) cudaEventDestroy(c->ev_f[i]);
+    }
+    for (int i = 0; i < 2; ++i) if (c->ev_sum[i]) cudaEventDestroy(c->ev_sum[i]);
+    if (c->ev_bin) cudaEventDestroy(c->ev_bin);
+    if (c->ev_c) cudaEventDestroy(c->ev_c);
+    for (int i = 0; i < 2; ++i) if (c->ev_run[i]) cudaEventDestroy(c->ev_run[i]);
+    if (c->s_c) cudaStreamDestroy(c->s_c);
+    if (c->s_main) cudaStreamDestroy(c->s_main);
+    delete c;
+    return HYTG_OK;
+}
+
+hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *offsets,
+                          const uint32_t *dst, const uint32_t *weights) {
+    if (!c) return HYTG_ERR_ARG;
+    try {
+        if (V == 0 || V > 0xFFFFFFFFull) return fail(c, HYTG_ERR_ARG, "V must be in [1, 2^32-1]");
+        if (!offsets || (E > 0 && !dst)) return fail(c, HYTG_ERR_ARG, "null CSR array");
+        if (offsets[0] != 0 || offsets[V] != E) return fail(c, HYTG_ERR_ARG, "offsets[0] must be 0 and offsets[V] must be E");
+        bool ok = true;
+        for (uint64_t v = 0; v < V && ok; ++v) ok = offsets[v] <= offsets[v + 1];
+        if (!ok) return fail(c, HYTG_ERR_ARG, "offsets must be non-decreasing");
+        {
+            std::vector<char> bad(16, 0);
+            std::atomic<bool> any_bad{false};
+            parallel_chunks(E, [&](uint64_t lo, uint64_t hi) {
+                for (uint64_t e = lo; e < hi; ++e)
+                    if (dst[e] >= V) { any_bad = true; return; }
+            });
+            if (any_bad) return fail(c, HYTG_ERR_ARG, "dst entry out of range");
+        }
+        CK(cudaSetDevice(c->device));
+        CK(cudaDeviceSynchronize());
+        free_graph(c);
+        if (getenv("HYTG_INJECT_HOSTMEM_FAIL") && atoi(getenv("HYTG_INJECT_HOSTMEM_FAIL")) != 0)
+            return fail(c, HYTG_ERR_HOSTMEM, "pinned allocation failure injected by HYTG_INJECT_HOSTMEM_FAIL");
+        const size_t eb = std::max<uint64_t>(E, 1) * 4;
+        if (cudaHostAlloc((void **)&c->h_dst, eb, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_dst = nullptr;
+            return fail(c, HYTG_ERR_HOSTMEM, "cudaHostAlloc of the neighbour array failed");
+        }
+        if (weights) {
+            if (cudaHostAlloc((void **)&c->h_w, eb, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                c->h_w = nullptr;
+                free_graph(c);
+                return fail(c, HYTG_ERR_HOSTMEM, "cudaHostAlloc of the weight array failed");
+            }
+        }
+        parallel_chunks(E, [&](uint64_t lo, uint64_t hi) {
+            memcpy(c->h_dst + lo, dst + lo, (hi - lo) * 4);
+            if (weights) memcpy(c->h_w + lo, weights + lo, (hi - lo) * 4);
+        });
+        void *mp = nullptr;
+        CK(cudaHostGetDevicePointer(&mp, c->h_dst, 0));
+        c->m_dst = (const uint32_t *)mp;
+        if (weights) {
+            CK(cudaHostGetDevicePointer(&mp, c->h_w, 0));
+            c->m_w = (const uint32_t *)mp;
+        }
+        c->V = V;
+        c->E = E;
+        c->weighted = weights != nullptr;
+        c->h_off.assign(offsets, offsets + V + 1);
+        c->part_edges = std::max<uint64_t>(1, (uint64_t)(c->part_bytes / 4));
+        make_partitions(c);
+        c->n_segs = (V + kSegVerts - 1) / kSegVerts;
+        c->n_words_alloc = c->n_segs * kSegWords;
+        CK(cudaMalloc(&c->d_off, (V + 1) * 8));
+        CK(cudaMemcpy(c->d_off, offsets, (V + 1) * 8, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c->d_val, V * 4));
+        CK(cudaMalloc(&c->d_delta, V * 4));
+        CK(cudaMalloc(&c->d_out, V * 4));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaMalloc(&c->d_bm[i], c->n_words_alloc * 4));
+            CK(cudaMemset(c->d_bm[i], 0, c->n_words_alloc * 4));
+        }
+        CK(cudaMalloc(&c->d_ebase, V * 8));
+        CK(cudaMalloc(&c->d_soff, V * 8));
+        CK(cudaMalloc(&c->d_pay, V * 4));
+        const uint64_t n_tiles = E / kTile + 8;
+        CK(cudaMalloc(&c->d_tiles, n_tiles * 4));
+        c->n_tiles_alloc = n_tiles;
+        CK(cudaMalloc(&c->d_seg, c->n_segs * 4 * 8));
+        hytg_status s = upload_partitions(c);
+        if (s != HYTG_OK) return s;
+        c->vertex_bytes = (V + 1) * 8 + 3 * V * 4 + 2 * c->n_words_alloc * 4 + V * 20 + n_tiles * 4 +
+                          c->n_segs * 32 + c->sum_dev_bytes;
+        c->loaded = true;
+        return HYTG_OK;
+    } catch (...) {
+        return fail(c, HYTG_ERR_HOSTMEM, "host allocation failed");
+    }
+}
+
+hytg_status hytg_set_device_budget(hytg_ctx *c, uint64_t bytes) {
+    if (!c) return HYTG_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaDeviceSynchronize());
+    dfree(c->d_pool);
+    c->budget = 0;
+    c->carve = Carve();
+    c->cache_filled_arrays = 0;
+    if (bytes == 0) return fail(c, HYTG_ERR_BUDGET, "zero budget");
+    CK(cudaMalloc(&c->d_pool, bytes + 8192));
+    c->budget = bytes;
+    if (c->loaded) {
+        hytg_status s = plan_carve(c, 1);
+        if (s == HYTG_ERR_BUDGET) {
+            // keep the pool; the error is reported again by hytg_run
+            return s;
+        }
+    }
+    return HYTG_OK;
+}
+
+hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
+    if (!c || !key) return HYTG_ERR_ARG;
+    std::string k(key);
+    auto bad = [&]() { return fail(c, HYTG_ERR_ARG, "bad value for parameter " + k); };
+    if (!std::isfinite(v)) return bad();
+    if (k == "alpha") { if (v < 0 || v > 1000) return bad(); c->alpha = v; }
+    else if (k == "beta") { if (v < 0 || v > 1000) return bad(); c->beta = v; }
+    else if (k == "gamma") { if (v < 0 || v > 1) return bad(); c->gamma = v; }
+    else if (k == "m") { if (v < 1 || v != std::floor(v)) return bad(); c->m = v; }
+    else if (k == "MR") { if (v < 1 || v != std::floor(v)) return bad(); c->MR = v; }
+    else if (k == "k") { if (v < 1 || v > 1024 || v != std::floor(v)) return bad(); c->k = v; c->carve = Carve(); }
+    else if (k == "part_bytes") {
+        if (v < 4 || v > 1e12) return bad();
+        c->part_bytes = v;
+        if (c->loaded) {
+            c->part_edges = std::max<uint64_t>(1, (uint64_t)(v / 4));
+            make_partitions(c);
+            hytg_status s = upload_partitions(c);
+            if (s != HYTG_OK) return s;
+        }
+    }
+    else if (k == "streams") { if (v < 1 || v > kMaxStreams || v != std::floor(v)) return bad(); c->streams = v; c->carve = Carve(); }
+    else if (k == "staging_frac") { if (v <= 0 || v >= 1) return bad(); c->staging_frac = v; c->carve = Carve(); }
+    else if (k == "compact_frac") { if (v <= 0 || v >= 1) return bad(); c->compact_frac = v; c->carve = Carve(); }
+    else if (k == "force_route") { if (!(v == -1 || (v >= 1 && v <= 5)) || v != std::floor(v)) return bad(); c->force_route = v; }
+    else if (k == "seed") { if (v < 0) return bad(); c->seed = v; }
+    else if (k == "pr_damping") { if (v <= 0 || v >= 1) return bad(); c->pr_damping = v; }
+    else if (k == "pr_eps") { if (v <= 0) return bad(); c->pr_eps = v; }
+    else if (k == "max_iters") { if (v < 1) return bad(); c->max_iters = v; }
+    else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
+    else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
+    return HYTG_OK;
+}
+
+hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
+    if (!c || !key || !v) return HYTG_ERR_ARG;
+    std::string k(key);
+    if (k == "alpha") *v = c->alpha;
+    else if (k == "beta") *v = c->beta;
+    else if (k == "gamma") *v = c->gamma;
+    else if (k == "m") *v = c->m;
+    else if (k == "MR") *v = c->MR;
+    else if (k == "k") *v = c->k;
+    else if (k == "part_bytes") *v = c->part_bytes;
+    else if (k == "streams") *v = c->streams;
+    else if (k == "staging_frac") *v = c->staging_frac;
+    else if (k == "compact_frac") *v = c->compact_frac;
+    else if (k == "force_route") *v = c->force_route;
+    else if (k == "seed") *v = c->seed;
+    else if (k == "pr_damping") *v = c->pr_damping;
+    else if (k == "pr_eps") *v = c->pr_eps;
+    else if (k == "max_iters") *v = c->max_iters;
+    else if (k == "timing") *v = c->timing;
+    else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
+    return HYTG_OK;
+}
+
+hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, uint32_t n_sources) {
+    if (!c) return HYTG_ERR_ARG;
+    const int algo = (int)algo_in;
+    if (algo < 0 || algo > 4) return fail(c, HYTG_ERR_ARG, "unknown algorithm");
+    if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
+    if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
+    const bool needs_src = (algo == kBFS || algo == kSSSP || algo == kPPR);
+    uint32_t source = 0;
+    if (needs_src) {
+        if (!sources || n_sources != 1)
+            return fail(c, HYTG_ERR_ARG, "this algorithm takes exactly one source");
+        source = sources[0];
+        if (source >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
+    }
+    if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
+    try {
+        CK(cudaSetDevice(c->device));
+        const auto t_start = std::chrono::steady_clock::now();
+        c->have_result = false;
+        c->stats = hytg_stats{};
+        c->iters.clear();
+        c->timed.clear();
+        c->ev_used = 0;
+        const int n_arrays = (algo == kSSSP) ? 2 : 1;
+        CK(cudaEventRecord(c->ev_run[0], c->s_main));
+        hytg_status s = plan_carve(c, n_arrays);
+        if (s != HYTG_OK) return s;
+        s = ensure_cache(c, n_arrays);
+        if (s != HYTG_OK) return s;
+        Carve &cv = c->carve;
+        int cur = 0;
+        CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
+        {
+            AlgoState st = algo_state(c, algo, cur);
+            ScopedTime t(c, HYTG_K_INIT, c->s_main);
+            CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
+        }
+        const SumLayout L = sum_layout((uint32_t)(c->part_vb.size() - 1));
+        const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+        const uint64_t ebytes = 4ull * n_arrays;
+        uint32_t it = 0;
+        s = issue_plan(c, algo, cur, it, 0, true);
+        if (s != HYTG_OK) return s;
+        std::vector<int> f_streams_used;
+        for (;;) {
+            const int buf = it & 1;
+            CK(cudaEventSynchronize(c->ev_sum[buf]));
+            const char *hb = (const char *)c->h_sumbuf[buf];
+            const Summary *hs = (const Summary *)hb;
+            if (hs->n_active == 0) break;
+            if (it >= (uint32_t)c->max_iters) { c->stats.status = HYTG_OK; break; }
+            const unsigned long long *p_edges = (const unsigned long long *)(hb + L.edges);
+            const unsigned long long *p_rentry = (const unsigned long long *)(hb + L.route_entry);
+            const unsigned long long *p_redge = (const unsigned long long *)(hb + L.route_edge);
+            const unsigned char *p_route = (const unsigned char *)(hb + L.route);
+            hytg_iter_record rec{};
+            rec.active_vertices = hs->n_active;
+            AlgoState st = algo_state(c, algo, cur);
+            ListArrays la = list_arrays(c);
+            Summary *dsum = (Summary *)c->d_sumbuf;
+            // --- F: task combination (Alg. 1, k consecutive partitions, slot capacity)
+            uint64_t f_bytes = 0;
+            uint32_t n_tasks = 0;
+            f_streams_used.clear();
+            uint32_t i = 0;
+            while (i < N) {
+                if (p_route[i] != kRouteF) { ++i; continue; }
+                uint32_t j = i;
+                uint64_t edges = c->part_eb[i + 1] - c->part_eb[i];
+                while (j + 1 < N && p_route[j + 1] == kRouteF && (j + 1 - i + 1) <= (uint32_t)c->k &&
+                       edges + (c->part_eb[j + 2] - c->part_eb[j + 1]) <= cv.slot_edges) {
+                    ++j;
+                    edges += c->part_eb[j + 1] - c->part_eb[j];
+                }
+                const uint32_t slot = n_tasks % cv.n_slots;
+                cudaStream_t fs = c->s_f[slot];
+                if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
+                    f_streams_used.push_back((int)slot);
+                    CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
+                }
+                const uint64_t e0 = c->part_eb[i];
+                {
+                    ScopedTime t(c, HYTG_K_COPY_F, fs);
+                    CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+                    if (n_arrays == 2)
+                        CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+                }
+                RelaxTask t{};
+                t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
+                t.shift = (long long)e0;
+                t.k_begin = p_redge[i];
+                t.k_end = p_redge[j] + p_edges[j];
+                t.first_entry = p_rentry[i];
+                t.device_sized = false;
+                t.src_len = edges;
+                {
+                    ScopedTime tm(c, HYTG_K_RELAX_F, fs);
+                    CK(launch_relax(st, la, dsum, t, 152 * 8, fs));
+                }
+                f_bytes += edges * ebytes;
+                ++n_tasks;
+                i = j + 1;
+            }
+            // --- C: gather active lists into the compaction buffer, relax, in chunks
+            const uint64_t c_edges = hs->route_edges[kRouteC];
+            if (c_edges) {
+                CK(cudaStreamWaitEvent(c->s_c, c->ev_bin, 0));
+                for (uint64_t cb = 0; cb < c_edges; cb += cv.compact_edges) {
+                    const uint64_t ce = std::min<uint64_t>(c_edges, cb + cv.compact_edges);
+                    RelaxTask g{};
+                    g.route = kRouteC; g.mode = kModeHost; g.dst = c->m_dst; g.w = c->m_w; g.shift = 0;
+                    g.k_begin = cb; g.k_end = ce; g.first_entry = 0; g.device_sized = false;
+                    g.src_len = c->E;
+                    {
+                        ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c);
+                        CK(launch_gather(la, dsum, g, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, 152 * 8, c->s_c));
+                    }
+                    RelaxTask r{};
+                    r.route = kRouteC; r.mode = kModeCompact; r.dst = cv.cmp_dst; r.w = cv.cmp_w;
+                    r.shift = (long long)cb; r.k_begin = cb; r.k_end = ce; r.first_entry = 0;
+                    r.device_sized = false;
+                    r.src_len = ce - cb;
+                    {
+                        ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
+                        CK(launch_relax(st, la, dsum, r, 152 * 8, c->s_c));
+                    }
+                }
+                CK(cudaEventRecord(c->ev_c, c->s_c));
+                CK(cudaStreamWaitEvent(c->s_main, c->ev_c, 0));
+            }
+            for (int sl : f_streams_used) {
+                CK(cudaEventRecord(c->ev_f[sl], c->s_f[sl]));
+                CK(cudaStreamWaitEvent(c->s_main, c->ev_f[sl], 0));
+            }
+            // --- statistics of this iteration
+            uint64_t act_edges = 0;
+            for (int r = 0; r < kRoutes; ++r) {
+                act_edges += hs->route_edges[r];
+                rec.route_partitions[r] = hs->route_parts[r];
+                rec.route_edges[r] = hs->route_edges[r];
+                c->stats.route_partitions[r] += hs->route_parts[r];
+                c->stats.route_vertices[r] += hs->route_entries[r];
+                c->stats.route_edges[r] += hs->route_edges[r];
+            }
+            const uint64_t zb = hs->route_lines[kRouteZ] * (uint64_t)c->m;
+            const uint64_t cbts = hs->route_lines[kRouteC] * (uint64_t)c->m;
+            c->stats.link_bytes[kRouteF] += f_bytes;
+            c->stats.link_bytes[kRouteZ] += zb;
+            c->stats.link_bytes[kRouteC] += cbts;
+            c->stats.f_tasks += n_tasks;
+            c->stats.edges_relaxed += act_edges;
+            c->stats.vertices_processed += hs->n_active;
+            rec.active_edges = act_edges;
+            rec.f_tasks = n_tasks;
+            rec.link_bytes = f_bytes + zb + cbts;
+            c->iters.push_back(rec);
+            // --- next iteration
+            cur ^= 1;
+            ++it;
+            s = issue_plan(c, algo, cur, it, it & 1, true);
+            if (s != HYTG_OK) return s;
+        }
+        c->stats.iterations = it;
+        // finalisation
+        if (algo == kPR || algo == kPPR) {
+            AlgoState st = algo_state(c, algo, cur);
+            ScopedTime t(c, HYTG_K_FINAL, c->s_main);
+            CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
+        }
+        unsigned int ovf = 0, ierr = 0;
+        double prs[2] = {0, 0};
+        CK(cudaMemcpyAsync(&ovf, c->d_overflow, 4, cudaMemcpyDeviceToHost, c->s_main));
+        CK(cudaMemcpyAsync(&ierr, c->d_err, 4, cudaMemcpyDeviceToHost, c->s_main));
+        if (algo == kPR || algo == kPPR)
+            CK(cudaMemcpyAsync(prs, c->d_prsums, 16, cudaMemcpyDeviceToHost, c->s_main));
+        CK(cudaEventRecord(c->ev_run[1], c->s_main));
+        CK(cudaStreamSynchronize(c->s_main));
+        CK(cudaGetLastError());
+        const auto t_end = std::chrono::steady_clock::now();
+        {
+            float dms = 0;
+            CK(cudaEventElapsedTime(&dms, c->ev_run[0], c->ev_run[1]));
+            c->stats.device_ms = dms;
+        }
+        c->stats.wall_ms = std::chrono::duration<double, std::milli>(t_end - t_start).count();
+        c->stats.pr_rank_sum = prs[0];
+        c->stats.pr_residual_sum = prs[1];
+        for (auto &tl : c->timed) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, tl.a, tl.b) == cudaSuccess) {
+                c->stats.kernel_ms[tl.kind] += ms;
+                c->stats.kernel_count[tl.kind] += 1;
+            }
+        }
+        cudaGetLastError();
+        c->last_algo = algo;
+        if (ierr) {
+            c->stats.status = HYTG_ERR_CUDA;
+            return fail(c, HYTG_ERR_CUDA, "internal index check failed (flags " + std::to_string(ierr) + ")");
+        }
+        if (ovf) {
+            c->stats.status = HYTG_ERR_OVERFLOW;
+            return fail(c, HYTG_ERR_OVERFLOW, "an SSSP distance does not fit in 32 bits");
+        }
+        c->have_result = true;
+        c->stats.status = HYTG_OK;
+        return HYTG_OK;
+    } catch (...) {
+        return fail(c, HYTG_ERR_HOSTMEM, "host allocation failed during the run");
+    }
+}
+
+hytg_status hytg_fetch_result(hytg_ctx *c, void *out, uint64_t out_bytes) {
+    if (!c || !out) return HYTG_ERR_ARG;
+    if (!c->have_result) return fail(c, HYTG_ERR_STATE, "no completed run");
+    if (out_bytes < c->V * 4) return fail(c, HYTG_ERR_ARG, "output buffer too small");
+    CK(cudaSetDevice(c->device));
+    const void *src = (c->last_algo == kPR || c->last_algo == kPPR) ? (const void *)c->d_out : (const void *)c->d_val;
+    CK(cudaMemcpyAsync(out, src, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaStreamSynchronize(c->s_main));
+    return HYTG_OK;
+}
+
+hytg_status hytg_fetch_pagerank_state(hytg_ctx *c, float *rank, float *delta, uint64_t V) {
+    if (!c) return HYTG_ERR_ARG;
+    if (!c->have_result || !(c->last_algo == kPR || c->last_algo == kPPR))
+        return fail(c, HYTG_ERR_STATE, "no completed PageRank run");
+    if (V < c->V) return fail(c, HYTG_ERR_ARG, "buffers too small");
+    CK(cudaSetDevice(c->device));
+    if (rank) CK(cudaMemcpyAsync(rank, c->d_val, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    if (delta) CK(cudaMemcpyAsync(delta, c->d_delta, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaStreamSynchronize(c->s_main));
+    return HYTG_OK;
+}
+
+hytg_status hytg_get_stats(hytg_ctx *c, hytg_stats *out) {
+    if (!c || !out) return HYTG_ERR_ARG;
+    *out = c->stats;
+    return HYTG_OK;
+}
+
+hytg_status hytg_get_info(hytg_ctx *c, hytg_info *out) {
+    if (!c || !out) return HYTG_ERR_ARG;
+    hytg_info i{};
+    i.V = c->V;
+    i.E = c->E;
+    i.weighted = c->weighted;
+    i.n_parts = c->loaded ? (uint32_t)(c->part_vb.size() - 1) : 0;
+    i.part_edges = c->part_edges;
+    i.slot_edges = c->carve.slot_edges;
+    i.n_slots = c->carve.n_slots;
+    i.n_cached = c->carve.n_cached;
+    i.budget_bytes = c->budget;
+    i.budget_used_bytes = c->carve.used;
+    i.compact_edges = c->carve.compact_edges;
+    i.vertex_state_bytes = c->loaded ? c->vertex_bytes : 0;
+    i.pinned_host_bytes = c->loaded ? std::max<uint64_t>(c->E, 1) * 4 * (c->weighted ? 2 : 1) : 0;
+    *out = i;
+    return HYTG_OK;
+}
+
+hytg_status hytg_get_partitions(hytg_ctx *c, uint64_t *vb, uint32_t cap, uint32_t *n_parts) {
+    if (!c || !n_parts) return HYTG_ERR_ARG;
+    if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    *n_parts = N;
+    if (vb) {
+        if (cap < N + 1) return fail(c, HYTG_ERR_ARG, "vbounds too small");
+        std::copy(c->part_vb.begin(), c->part_vb.end(), vb);
+    }
+    return HYTG_OK;
+}
+
+hytg_status hytg_plan(hytg_ctx *c, hytg_algo algo_in, const uint8_t *active, uint8_t *routes,
+                      uint64_t *counts, uint32_t cap) {
+    if (!c || !active || !routes) return HYTG_ERR_ARG;
+    const int algo = (int)algo_in;
+    if (algo < 0 || algo > 4) return fail(c, HYTG_ERR_ARG, "unknown algorithm");
+    if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
+    if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    if (cap < N) return fail(c, HYTG_ERR_ARG, "output arrays too small");
+    CK(cudaSetDevice(c->device));
+    hytg_status s = plan_carve(c, algo == kSSSP ? 2 : 1);
+    if (s != HYTG_OK) return s;
+    unsigned char *d_act = nullptr;
+    CK(cudaMalloc(&d_act, c->V));
+    cudaError_t e = cudaMemcpyAsync(d_act, active, c->V, cudaMemcpyHostToDevice, c->s_main);
+    if (e == cudaSuccess) e = launch_upload_bitmap(d_act, c->d_bm[0], c->V, c->n_words_alloc, c->s_main);
+    if (e != cudaSuccess) { cudaFree(d_act); return fail(c, HYTG_ERR_CUDA, cudaGetErrorString(e)); }
+    c->have_result = false;
+    s = issue_plan(c, algo, 0, 0, 0, false);
+    cudaStreamSynchronize(c->s_main);
+    cudaFree(d_act);
+    if (s != HYTG_OK) return s;
+    CK(cudaGetLastError());
+    const SumLayout L = sum_layout(N);
+    const char *hb = (const char *)c->h_sumbuf[0];
+    memcpy(routes, hb + L.route, N);
+    if (counts) {
+        const unsigned long long *na = (const unsigned long long *)(hb + L.n_act);
+        const unsigned long long *ed = (const unsigned long long *)(hb + L.edges);
+        const unsigned long long *ln = (const unsigned long long *)(hb + L.lines);
+        for (uint32_t p = 0; p < N; ++p) {
+            counts[3 * p] = na[p];
+            counts[3 * p + 1] = ed[p];
+            counts[3 * p + 2] = ln[p];
+        }
+    }
+    CK(cudaMemset(c->d_bm[0], 0, c->n_words_alloc * 4));
+    return HYTG_OK;
+}
+
+hytg_status hytg_probe_link(hytg_ctx *c, uint64_t bytes, uint32_t reps, double *memcpy_gbs,
+                            double *zerocopy_gbs) {
+    if (!c || bytes < 4096 || reps == 0) return HYTG_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    bytes &= ~uint64_t(511);
+    void *h = nullptr, *d = nullptr;
+    unsigned long long *sink = nullptr;
+    if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HYTG_ERR_HOSTMEM, "probe pinned allocation failed");
+    }
+    memset(h, 1, bytes);
+    cudaEvent_t a, b;
+    hytg_status st = HYTG_OK;
+    auto run = [&]() -> hytg_status {
+        CK(cudaMalloc(&d, bytes));
+        CK(cudaMalloc(&sink, 8));
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        void *mp = nullptr;
+        CK(cudaHostGetDevicePointer(&mp, h, 0));
+        float best = 1e30f;
+        for (uint32_t r = 0; r < reps + 1; ++r) {
+            CK(cudaEventRecord(a, c->s_main));
+            CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->s_main));
+            CK(cudaEventRecord(b, c->s_main));
+            CK(cudaEventSynchronize(b));
+            float ms;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (r > 0) best = std::min(best, ms);
+        }
+        if (memcpy_gbs) *memcpy_gbs = bytes / (best * 1e-3) / 1e9;
+        best = 1e30f;
+        for (uint32_t r = 0; r < reps + 1; ++r) {
+            CK(cudaEventRecord(a, c->s_main));
+            CK(launch_zc_probe((const uint4 *)mp, bytes / 16, sink, 152 * 8, c->s_main));
+            CK(cudaEventRecord(b, c->s_main));
+            CK(cudaEventSynchronize(b));
+            float ms;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (r > 0) best = std::min(best, ms);
+        }
+        if (zerocopy_gbs) *zerocopy_gbs = bytes / (best * 1e-3) / 1e9;
+        return HYTG_OK;
+    };
+    st = run();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (d) cudaFree(d);
+    if (sink) cudaFree(sink);
+    cudaFreeHost(h);
+    return st;
+}
+
+hytg_status hytg_get_iterations(hytg_ctx *c, hytg_iter_record *out, uint32_t cap, uint32_t *n) {
+    if (!c || !n) return HYTG_ERR_ARG;
+    *n = (uint32_t)c->iters.size();
+    if (out) {
+        const uint32_t k = std::min<uint32_t>(cap, *n);
+        std::copy(c->iters.begin(), c->iters.begin() + k, out);
+    }
+    return HYTG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// Push relax kernels over the active edges of one route (Sec. II-A push
+// model; Sec. VI-C processing kernels), and the compaction gather of the C
+// route (Sec. II-B ExpTM-compaction, here done by the GPU over the host link).
+//
+// Load balancing: the active vertices of a route form a list ordered by
+// vertex id; their out-edges form one "route edge space" [0, E_route).  A
+// block takes a tile of kTile consecutive route edges, finds the list entries
+// that own them (the entry holding the tile's first edge comes from the
+// tile index written by k_bin), marks each entry's first edge in shared
+// memory and fills the gaps with a max-scan, so every thread knows the owner
+// of each of its edges in O(1).  Threads take edges k0 + tid + j * 256, so a
+// warp reads consecutive edges of the same or adjacent lists: 128-byte lines
+// when the lists are long, and neighbouring lists share lines when
+// consecutive vertices are active.
+//
+// Edge sources (the route's transfer method):
+//   host    zero-copy loads from pinned, device-mapped host memory (Eq. 3 route);
+//   device  a device copy starting at CSR edge `shift` (cache and F routes:
+//           the partition's edges are shifted by its first edge index);
+//   compact the compacted buffer, where route edge k sits at k - shift.
+#include "common.cuh"
+
+namespace hytg {
+
+namespace {
+
+constexpr unsigned int kInf = 0xFFFFFFFFu;
+
+struct TileSmem {
+    long long delta[kTile + 1];          // edge address = k + delta
+    unsigned int pay[kTile + 1];
+    unsigned short sid[kTile];           // owner entry (tile-relative) of each slot
+    unsigned int wmax[kRelaxBlock / 32];
+};
+
+// Set up one tile; returns the number of edges (0 if nothing to do).
+__device__ __forceinline__ int tile_setup(TileSmem &sm, const ListArrays &la, const Summary *sum,
+                                          const RelaxTask &t, unsigned long long tile,
+                                          unsigned long long kb, unsigned long long ke,
+                                          unsigned long long *k0_out) {
+    const int r = t.route;
+    const unsigned long long rbase = sum->route_entry_base[r];
+    const unsigned long long tbase = sum->route_tile_base[r];
+    const unsigned long long n_ent = sum->route_entries[r];
+    const unsigned long long route_edges = sum->route_edges[r];
+    const unsigned long long tstart = tile * kTile;
+    const unsigned long long k0 = tstart > kb ? tstart : kb;
+    const unsigned long long tend = tstart + kTile;
+    const unsigned long long k1 = tend < ke ? tend : ke;
+    const unsigned long long i0 = (k0 == tstart) ? la.tile_first[tbase + tile] : t.first_entry;
+    const unsigned long long last_tile = (route_edges - 1) / kTile;
+    const unsigned long long i_last = (tile < last_tile) ? la.tile_first[tbase + tile + 1] : n_ent - 1;
+    const long long n_e_ll = (long long)i_last - (long long)i0 + 1;
+    if (n_e_ll < 1 || n_e_ll > kTile + 1 || i0 >= n_ent || i_last >= n_ent || k1 <= k0) {
+        // inconsistent tile index: record it and skip the tile (block-uniform)
+        if (threadIdx.x == 0) atomicOr(la.err, 1u);
+        *k0_out = k0;
+        return 0;
+    }
+    const int n_e = (int)n_e_ll;
+    const int n_slots = (int)(k1 - k0);
+    for (int j = threadIdx.x; j < kTile; j += kRelaxBlock) sm.sid[j] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_e; j += kRelaxBlock) {
+        const unsigned long long i = rbase + i0 + j;
+        const unsigned long long eb = la.ebase[i];
+        long long d;
+        if (t.mode == kModeCompact) d = -t.shift;
+        else d = (long long)la.soff[i] - (long long)eb - t.shift;
+        sm.delta[j] = d;
+        sm.pay[j] = la.pay[i];
+        if (j > 0) {
+            const long long head = (long long)eb - (long long)k0;
+            if (head > 0 && head < n_slots) sm.sid[head] = (unsigned short)j;
+            else if (head <= 0) atomicOr(la.err, 4u);
+        }
+    }
+    __syncthreads();
+    // inclusive max-scan of sid over the tile (8 consecutive slots per thread)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int base = threadIdx.x * kRelaxIPT;
+    unsigned int mx = 0;
+#pragma unroll
+    for (int q = 0; q < kRelaxIPT; ++q) {
+        unsigned int x = sm.sid[base + q];
+        mx = x > mx ? x : mx;
+        sm.sid[base + q] = (unsigned short)mx;
+    }
+    unsigned int inc = mx;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = y > inc ? y : inc;
+    }
+    if (lane == 31) sm.wmax[wid] = inc;
+    __syncthreads();
+    unsigned int carry = 0;
+    for (int q = 0; q < wid; ++q) carry = sm.wmax[q] > carry ? sm.wmax[q] : carry;
+    unsigned int excl = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane > 0) carry = excl > carry ? excl : carry;
+    if (carry) {
+#pragma unroll
+        for (int q = 0; q < kRelaxIPT; ++q)
+            if (sm.sid[base + q] < carry) sm.sid[base + q] = (unsigned short)carry;
+    }
+    __syncthreads();
+    *k0_out = k0;
+    return n_slots;
+}
+
+template <int ALGO>
+__device__ __forceinline__ void relax_edge(const AlgoState &st, unsigned int v, unsigned int pay,
+                                           unsigned int w) {
+    if (ALGO == kPR || ALGO == kPPR) {
+        const float msg = __uint_as_float(pay);
+        const float old = atomicAdd(&st.delta[v], msg);
+        if (old <= st.eps && old + msg > st.eps) atomicOr(&st.bm_next[v >> 5], 1u << (v & 31));
+    } else {
+        unsigned int nv;
+        if (ALGO == kBFS) {
+            nv = pay + 1u;
+        } else if (ALGO == kSSSP) {
+            const unsigned long long s = (unsigned long long)pay + w;
+            if (s >= 0xFFFFFFFEull) { *st.overflow = 1u; return; }
+            nv = (unsigned int)s;
+        } else {
+            nv = pay;
+        }
+        if (nv < __ldcg(&st.val[v])) {
+            const unsigned int old = atomicMin(&st.val[v], nv);
+            if (nv < old) atomicOr(&st.bm_next[v >> 5], 1u << (v & 31));
+        }
+    }
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays la,
+                                                       const Summary *sum, RelaxTask t) {
+    __shared__ TileSmem sm;
+    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
+    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    if (kb >= ke) return;
+    const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
+    const bool weighted = (ALGO == kSSSP);
+    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
+        unsigned long long k0;
+        const int n = tile_setup(sm, la, sum, t, tile, kb, ke, &k0);
+        unsigned int dv[kRelaxIPT], wv[kRelaxIPT], pv[kRelaxIPT];
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j) {
+            const int slot = threadIdx.x + j * kRelaxBlock;
+            dv[j] = kInf;
+            wv[j] = 0;
+            pv[j] = 0;
+            if (slot < n) {
+                const int i = sm.sid[slot];
+                const long long e = (long long)(k0 + slot) + sm.delta[i];
+                if (e >= 0 && (unsigned long long)e < t.src_len) {
+                    dv[j] = __ldg(t.dst + e);
+                    if (weighted) wv[j] = __ldg(t.w + e);
+                    pv[j] = sm.pay[i];
+                } else {
+                    atomicOr(la.err, 8u);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j)
+            if (dv[j] != kInf) relax_edge<ALGO>(st, dv[j], pv[j], wv[j]);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Summary *sum,
+                                                        RelaxTask t, unsigned int *out_dst,
+                                                        unsigned int *out_w) {
+    __shared__ TileSmem sm;
+    const unsigned long long kb = t.k_begin, ke = t.k_end;
+    if (kb >= ke) return;
+    const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
+    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
+        unsigned long long k0;
+        const int n = tile_setup(sm, la, sum, t, tile, kb, ke, &k0);
+        unsigned int dv[kRelaxIPT], wv[kRelaxIPT];
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j) {
+            const int slot = threadIdx.x + j * kRelaxBlock;
+            dv[j] = 0;
+            wv[j] = 0;
+            if (slot < n) {
+                const long long e = (long long)(k0 + slot) + sm.delta[sm.sid[slot]];
+                if (e >= 0 && (unsigned long long)e < t.src_len) {
+                    dv[j] = __ldg(t.dst + e);
+                    if (out_w) wv[j] = __ldg(t.w + e);
+                } else {
+                    atomicOr(la.err, 8u);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j) {
+            const int slot = threadIdx.x + j * kRelaxBlock;
+            if (slot < n) {
+                const unsigned long long o = k0 + slot - kb;
+                out_dst[o] = dv[j];
+                if (out_w) out_w[o] = wv[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
+                         const RelaxTask &t, int grid_cap, cudaStream_t s) {
+    unsigned int grid = (unsigned int)grid_cap;
+    if (!t.device_sized) {
+        if (t.k_begin >= t.k_end) return cudaSuccess;
+        const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
+        if (tiles < grid) grid = (unsigned int)tiles;
+    }
+    switch (st.algo) {
+        case kBFS: k_relax<kBFS><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
+        case kSSSP: k_relax<kSSSP><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
+        case kCC: k_relax<kCC><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
+        default: k_relax<kPR><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
+                          unsigned int *out_dst, unsigned int *out_w, int grid_cap,
+                          cudaStream_t s) {
+    if (t.k_begin >= t.k_end) return cudaSuccess;
+    const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
+    unsigned int grid = tiles < (unsigned long long)grid_cap ? (unsigned int)tiles : (unsigned int)grid_cap;
+    k_gather<<<grid, kRelaxBlock, 0, s>>>(la, sum, t, out_dst, out_w);
+    return cudaGetLastError();
+}
+
+}  // namespace hytg

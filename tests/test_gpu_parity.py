@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+BFS levels, SSSP distances and CC labels must be bit-exact; PageRank and
+personalised PageRank within 1e-4 in L1 of the normalised vectors (the
+tolerance the task sets for FP32 delta-PageRank against the FP64 oracle).
+Every route is exercised alone (forced), at random per partition and
+iteration, and under the cost model; results must not depend on the route.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from gen import graphgen as gg
+from oracle import oracle as orc
+from oracle import planner as pl
+
+pytestmark = pytest.mark.gpu
+
+PR_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hy():
+    from paper_2208_14935_gb300 import build, hytg
+    build.build()
+    hytg.load()
+    return hytg
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    return gg.rmat(16, seed=1)
+
+
+@pytest.fixture(scope="module")
+def rmat16_sym(rmat16):
+    return gg.symmetrize(rmat16)
+
+
+def edge_bytes(g, algo):
+    return g.E * (8 if algo == "sssp" else 4)
+
+
+def engine(hy, g, budget, **params):
+    e = hy.Engine(params={"part_bytes": 64 * 1024, **params})
+    e.load(g)
+    e.set_budget(int(budget))
+    return e
+
+
+def check(g, algo, got, src=0):
+    if algo == "bfs":
+        want, _ = orc.bfs(g, src)
+        assert np.array_equal(got, want), f"BFS mismatch at {np.flatnonzero(got != want)[:10]}"
+    elif algo == "sssp":
+        want, _, _ = orc.sssp(g, src)
+        assert np.array_equal(got, want), f"SSSP mismatch at {np.flatnonzero(got != want)[:10]}"
+    elif algo == "cc":
+        want = orc.cc(g)
+        assert np.array_equal(got, want), f"CC mismatch at {np.flatnonzero(got != want)[:10]}"
+    elif algo == "pagerank":
+        x, _, _ = orc.pagerank(g, tol=1e-13)
+        err = float(np.abs(got.astype(np.float64) - x).sum())
+        assert err <= PR_TOL, f"PageRank L1 {err}"
+        assert abs(float(got.astype(np.float64).sum()) - 1.0) < 1e-5
+    elif algo == "ppr":
+        x, _, _ = orc.pagerank(g, tol=1e-13, seed=src)
+        err = float(np.abs(got.astype(np.float64) - x).sum())
+        assert err <= PR_TOL, f"PPR L1 {err}"
+
+
+FORCE = [-1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank", "ppr"])
+@pytest.mark.parametrize("force", FORCE)
+def test_rmat16_routes(hy, rmat16, algo, force):
+    """R-MAT scale 16, budget 25 % of the edge bytes the algorithm reads."""
+    e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, force_route=force, seed=7)
+    src = 0 if algo != "ppr" else 5
+    got = e.run(algo, None if algo == "pagerank" else src)
+    check(rmat16, algo, got, src)
+    st = e.stats()
+    assert st["edges_relaxed"] > 0
+    if force in (2, 3, 4):
+        others = [r for r in (1, 2, 3, 4) if r != force]
+        assert st["route_partitions"][force] > 0
+        assert all(st["route_partitions"][r] == 0 for r in others)
+    e.close()
+
+
+@pytest.mark.parametrize("force", FORCE)
+def test_rmat16_cc(hy, rmat16_sym, force):
+    e = engine(hy, rmat16_sym, edge_bytes(rmat16_sym, "cc") // 4, force_route=force, seed=3)
+    check(rmat16_sym, "cc", e.run("cc"))
+    e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
+def test_all_cached(hy, rmat16, algo):
+    """A budget larger than the graph: every partition resident (cache route only)."""
+    e = engine(hy, rmat16, 4 * edge_bytes(rmat16, algo), force_route=1)
+    got = e.run(algo, None if algo == "pagerank" else 0)
+    check(rmat16, algo, got)
+    st = e.stats()
+    assert st["route_partitions"][1] > 0
+    assert sum(st["route_partitions"][2:]) == 0
+    assert e.info()["n_cached"] == e.info()["n_parts"]
+    e.close()
+
+
+def test_all_four_routes_fire_under_cost_model(hy, rmat16):
+    """With a small MR the cost model uses cache, F, C and Z across SSSP iterations."""
+    e = engine(hy, rmat16, edge_bytes(rmat16, "sssp") // 4, MR=4)
+    check(rmat16, "sssp", e.run("sssp", 0))
+    rp = e.stats()["route_partitions"]
+    assert all(rp[r] > 0 for r in (1, 2, 3, 4)), rp
+    e.close()
+
+
+IRREGULAR = [
+    dict(V=1, E=0), dict(V=1, E=3), dict(V=33, E=100), dict(V=1000, E=1), dict(V=4097, E=30000),
+    dict(V=5000, E=80000, skew=1.3), dict(V=12345, E=200000, skew=0.9),
+]
+
+
+@pytest.mark.parametrize("spec", IRREGULAR, ids=lambda s: f"V{s['V']}E{s['E']}")
+@pytest.mark.parametrize("force", [-1, 2, 3, 4, 5])
+def test_irregular_graphs(hy, spec, force):
+    g = gg.random_graph(spec["V"], spec["E"], seed=spec["V"] + spec["E"], skew=spec.get("skew", 0.0))
+    s = gg.symmetrize(g)
+    budget = max(64 * 1024, g.E * 2)
+    e = engine(hy, g, budget, force_route=force, part_bytes=4096, seed=11)
+    srcs = sorted({0, g.V - 1, g.V // 2})
+    for src in srcs:
+        check(g, "bfs", e.run("bfs", src), src)
+        check(g, "sssp", e.run("sssp", src), src)
+    if g.V > 1:
+        check(g, "pagerank", e.run("pagerank"))
+    e.close()
+    e = engine(hy, s, max(64 * 1024, s.E * 2), force_route=force, part_bytes=4096, seed=12)
+    check(s, "cc", e.run("cc"))
+    e.close()
+
+
+def test_hub_larger_than_partition(hy):
+    """A star whose centre alone exceeds the partition size (single-word partition)."""
+    L = 50000
+    off = np.zeros(L + 2, np.uint64)
+    off[1:] = L
+    off[-1] = L + 0
+    dst = np.arange(1, L + 1, dtype=np.uint32)
+    g = gg.CSR(L + 1, L, off, dst, np.full(L, 3, np.uint32))
+    e = engine(hy, g, 8 * L * 4, part_bytes=4096)
+    vb = e.partitions()
+    assert vb[1] == 32  # the centre's word forms a partition with more than part_edges edges
+    for force in (-1, 2, 3, 4):
+        e.set_param("force_route", force)
+        check(g, "bfs", e.run("bfs", 0))
+        check(g, "sssp", e.run("sssp", 0))
+    e.close()
+
+
+def test_mesh_high_diameter(hy):
+    g = gg.mesh(256, 128, shortcut_frac=0.001, radius=16, wmax=1000)
+    e = engine(hy, g, g.E * 8 // 5, part_bytes=16384)   # 20 % of dst + weight bytes
+    check(g, "bfs", e.run("bfs", 0))
+    check(g, "sssp", e.run("sssp", 0))
+    check(g, "cc", e.run("cc"))
+    assert e.stats()["iterations"] > 20
+    e.close()
+
+
+def test_partition_table_matches_oracle(hy, rmat16):
+    for pb in (4096, 64 * 1024, 1 << 20, 4 << 20):
+        e = engine(hy, rmat16, 1 << 24, part_bytes=pb)
+        assert e.partitions().tolist() == pl.partition_bounds(rmat16.off, pb // 4)
+        e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp"])
+def test_planner_matches_oracle(hy, rmat16, algo):
+    """Cost analysis and engine selection on the device (Alg. 1) against the
+    exact-rational oracle, on random frontiers of several densities."""
+    params = dict(alpha=0.8, beta=0.4, gamma=0.625, MR=8)
+    e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, **params)
+    vb = e.partitions()
+    E_part = np.diff(rmat16.off[vb.astype(np.int64)].astype(np.int64))
+    rng = np.random.default_rng(5)
+    d1 = 8 if algo == "sssp" else 4
+    n_arrays = 2 if algo == "sssp" else 1
+    for dens in (1e-4, 1e-3, 0.01, 0.1, 0.5, 1.0):
+        act = (rng.random(rmat16.V) < dens).astype(np.uint8)
+        routes, counts = e.plan(algo, act)
+        na, ae, ln = orc.partition_counts(rmat16, act, vb, 4, n_arrays, 128)
+        assert np.array_equal(counts[:, 0], na) and np.array_equal(counts[:, 1], ae)
+        assert np.array_equal(counts[:, 2], ln)
+        n_cached = e.info()["n_cached"]
+        want = pl.plan(E_part, na, ae, ln, d1, resident=range(n_cached), m=128, MR=8,
+                       alpha=Fraction("0.8"), beta=Fraction("0.4"), gamma=Fraction("0.625"))
+        assert routes.tolist() == want, dens
+    e.close()
+
+
+def test_budget_and_argument_errors(hy, rmat16):
+    e = hy.Engine(params={"part_bytes": 64 * 1024})
+    e.load(rmat16)
+    with pytest.raises(hy.HytgError) as ex:
+        e.set_budget(1024)
+    assert ex.value.status == hy.HYTG_ERR_BUDGET
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("bfs", 0)
+    assert ex.value.status in (hy.HYTG_ERR_BUDGET, hy.HYTG_ERR_STATE)
+    e.set_budget(1 << 22)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("bfs", rmat16.V)
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    with pytest.raises(hy.HytgError) as ex:
+        e.set_param("no_such_key", 1)
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    check(rmat16, "bfs", e.run("bfs", 0))    # context still usable after errors
+    e.close()
+    g = gg.random_graph(100, 300, seed=1, weights=False)
+    e = engine(hy, g, 1 << 20)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("sssp", 0)
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    e.close()
+
+
+def test_sssp_overflow(hy):
+    g = gg.CSR(4, 3, np.array([0, 1, 2, 3, 3], np.uint64), np.array([1, 2, 3], np.uint32),
+               np.array([0x7FFFFFFF, 0x7FFFFFFF, 5], np.uint32))
+    e = engine(hy, g, 1 << 20)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("sssp", 0)
+    assert ex.value.status == hy.HYTG_ERR_OVERFLOW
+    check(g, "bfs", e.run("bfs", 0))
+    e.close()
+
+
+def test_invalid_csr_rejected(hy):
+    g = gg.random_graph(50, 100, seed=2)
+    bad = gg.CSR(g.V, g.E, g.off.copy(), g.dst.copy(), g.w)
+    bad.dst[3] = g.V
+    e = hy.Engine()
+    with pytest.raises(hy.HytgError) as ex:
+        e.load(bad)
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    e.close()
+
+
+def test_pagerank_bound_reported(hy, rmat16):
+    e = engine(hy, rmat16, edge_bytes(rmat16, "pagerank") // 4)
+    got = e.run("pagerank")
+    check(rmat16, "pagerank", got)
+    st = e.stats()
+    rank, delta = e.pagerank_state()
+    B = st["pr_residual_sum"] / ((1 - 0.85) * st["pr_rank_sum"])
+    assert B < 1e-4
+    assert abs(float(rank.astype(np.float64).sum()) - st["pr_rank_sum"]) < 1e-3 * st["pr_rank_sum"]
+    e.close()
