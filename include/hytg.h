@@ -207,6 +207,55 @@ hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t c
 const char *hytg_status_str(hytg_status s);
 const char *hytg_last_error(hytg_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free planning (this entry point has no counterpart in the paper).
+ *
+ * Some callers cannot call cudaMalloc: code that runs while a stream is being
+ * captured into a CUDA graph (allocation is not a capturable operation),
+ * code embedded in a framework whose caching allocator owns all device
+ * memory, or a service that must not change its device footprint once it has
+ * started.  hytg_plan_noalloc gives them the per-partition counting and
+ * engine selection of hytg_plan (Sec. V-A, Eq. 1-3) without any allocation:
+ * no context, no cudaMalloc/cudaFree and no allocating library call.  Its only
+ * scratch is a static device array of HYTG_NOALLOC_MAX_PARTS + 1 partition
+ * bounds (about 768 KiB), which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * All pointers are device pointers owned by the caller:
+ *   frontier      ceil(V / 32) uint32 words, bit v % 32 of word v / 32 set
+ *                 when vertex v is active; bits at or beyond V are ignored;
+ *   offsets       V + 1 uint64 CSR row offsets;
+ *   part_vbounds  n_parts + 1 uint64 vertex bounds of the partitions, from 0
+ *                 to V, on multiples of 32 except the last (the layout that
+ *                 hytg_get_partitions returns);
+ *   routes        n_parts uint8 outputs (hytg_route);
+ *   counts        3 * n_parts uint64 outputs {|A_i|, active edges, 128-byte
+ *                 lines} per partition (zeroed by the call itself).
+ * Partitions [0, n_cached) count as resident.  params may be NULL for the
+ * paper's constants (alpha 0.8, beta 0.4, gamma 0.625, m 128, MR 256).
+ * stream is a cudaStream_t (NULL: the default stream); the work is queued on
+ * it and the call returns without waiting.
+ *
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, so calls that
+ * overlap on the GPU (on different streams, or from several threads) race:
+ * order them on one stream.  Errors: HYTG_ERR_ARG for a NULL pointer, an
+ * unknown algorithm, V outside [1, 2^32 - 1], n_parts of 0 or above
+ * HYTG_NOALLOC_MAX_PARTS, n_cached > n_parts or bad params; HYTG_ERR_CUDA if
+ * the address lookup or a launch fails. */
+#define HYTG_NOALLOC_MAX_PARTS 65536u
+
+typedef struct hytg_cost_params {
+    double alpha, beta, gamma;   /* selection thresholds and RTT_zc factor */
+    uint32_t m, MR;              /* request bytes, outstanding requests */
+} hytg_cost_params;
+
+hytg_status hytg_plan_noalloc(hytg_algo algo, const uint32_t *frontier, const uint64_t *offsets,
+                              uint64_t V, const uint64_t *part_vbounds, uint32_t n_parts,
+                              uint32_t n_cached, const hytg_cost_params *params, uint8_t *routes,
+                              uint64_t *counts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 //             and the tile index of the load-balanced relax kernels, takes the
 //             delta of delta-PageRank, and clears the consumed bitmap.
 #include "common.cuh"
+#include "cost_model.cuh"
 
 namespace hytg {
 
@@ -123,45 +124,14 @@ __device__ void block_scan_excl(unsigned long long (&v)[K], unsigned long long (
     __syncthreads();
 }
 
-__device__ int decide_route(unsigned int p, const GraphDev &g, const PartArrays &pa,
-                            const CostParams &cp) {
-    const unsigned long long Ae = pa.edges[p];
-    if (Ae == 0) return kRouteNone;
-    const bool resident = p < cp.n_cached;
-    if (cp.force_route == kRouteCache && resident) return kRouteCache;
-    if (cp.force_route == kRouteF || cp.force_route == kRouteC || cp.force_route == kRouteZ)
-        return cp.force_route;
-    if (cp.force_route == 5) {
-        const unsigned long long h =
-            mix64(cp.seed ^ mix64(((unsigned long long)cp.iteration << 32) | p));
-        if (resident) return 1 + (int)(h % 4ull);   // cache, F, C, Z
-        return 2 + (int)(h % 3ull);                 // F, C, Z
-    }
-    if (resident) return kRouteCache;
-    // Eq. 1-3 with RTT = 1; exact integer comparisons.
-    typedef unsigned __int128 u128;
-    const unsigned long long Ei = g.part_eb[p + 1] - g.part_eb[p];
-    const unsigned long long A = pa.n_act[p], L = pa.lines[p];
-    const unsigned long long den = cp.m * cp.MR;
-    const u128 Tef = ((u128)Ei * cp.d1 + den - 1) / den;
-    const u128 Tec = ((u128)Ae * cp.d1 + (u128)A * cp.d2 + den - 1) / den;
-    const u128 Tl = ((u128)L + cp.MR - 1) / cp.MR;
-    // Tiz = Tl * (gamma + (1 - gamma) * Ae / Ei) = TizN / TizD
-    const u128 TizN = Tl * ((u128)cp.gamma_num * Ei + (u128)(kParamDen - cp.gamma_num) * Ae);
-    const u128 TizD = (u128)kParamDen * Ei;
-    const bool c1 = (u128)kParamDen * Tec < (u128)cp.alpha_num * Tef;
-    const bool c2 = (u128)kParamDen * Tec * TizD < (u128)cp.beta_num * TizN;
-    if (c1 && c2) return kRouteC;
-    if (Tef * TizD < TizN) return kRouteF;
-    return kRouteZ;
-}
-
 __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays pa, SegArrays sa,
                                                          CostParams cp, Summary *sum) {
     __shared__ unsigned long long smem[33 * 12];
     const unsigned int N = g.N;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (unsigned int p = tid; p < N; p += nt) pa.route[p] = (unsigned char)decide_route(p, g, pa, cp);
+    for (unsigned int p = tid; p < N; p += nt)
+        pa.route[p] = (unsigned char)decide_route_counts(p, g.part_eb[p + 1] - g.part_eb[p], pa.n_act[p],
+                                                         pa.edges[p], pa.lines[p], cp);
     __syncthreads();
 
     // per-route and global prefixes over partitions (contiguous chunk per thread)

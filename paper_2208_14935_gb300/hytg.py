@@ -52,6 +52,10 @@ class hytg_iter_record(ctypes.Structure):
                 ("f_tasks", u32), ("route_edges", u64 * 5), ("link_bytes", u64)]
 
 
+class hytg_cost_params(ctypes.Structure):
+    _fields_ = [("alpha", dbl), ("beta", dbl), ("gamma", dbl), ("m", u32), ("MR", u32)]
+
+
 class HytgError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"hytg status {status}: {msg}")
@@ -94,6 +98,8 @@ def load(path: Optional[str] = None):
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = i32
+        lib.hytg_plan_noalloc.argtypes = [i32, vp, vp, u64, vp, u32, u32, P(hytg_cost_params), vp, vp, vp]
+        lib.hytg_plan_noalloc.restype = i32
         lib.hytg_status_str.argtypes = [i32]
         lib.hytg_status_str.restype = ctypes.c_char_p
         lib.hytg_last_error.argtypes = [vp]
@@ -195,6 +201,21 @@ def hytg_plan(ctx, algo: int, active: np.ndarray, n_parts: int):
     counts = np.empty(3 * n_parts, np.uint64)
     _check(ctx, load().hytg_plan(ctx, int(algo), _ptr(act), _ptr(routes), _ptr(counts), n_parts))
     return routes, counts.reshape(n_parts, 3)
+
+
+def hytg_plan_noalloc(algo: int, frontier_ptr: int, offsets_ptr: int, V: int, vbounds_ptr: int,
+                      n_parts: int, n_cached: int, routes_ptr: int, counts_ptr: int,
+                      params: Optional[Dict[str, float]] = None, stream: int = 0) -> int:
+    """Allocation-free planning on caller-owned device buffers (pointers as
+    integers); returns the hytg_status without raising."""
+    prm = None
+    if params is not None:
+        prm = hytg_cost_params(params.get("alpha", 0.8), params.get("beta", 0.4),
+                               params.get("gamma", 0.625), int(params.get("m", 128)),
+                               int(params.get("MR", 256)))
+    return load().hytg_plan_noalloc(int(algo), vp(frontier_ptr), vp(offsets_ptr), V, vp(vbounds_ptr),
+                                    n_parts, n_cached, None if prm is None else ctypes.byref(prm),
+                                    vp(routes_ptr), vp(counts_ptr), vp(stream) if stream else None)
 
 
 def hytg_probe_link(ctx, nbytes: int = 1 << 30, reps: int = 10):
