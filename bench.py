@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timing", action="store_true", help="skip per-kernel CUDA events")
     ap.add_argument("--param", action="append", default=[], help="key=value engine parameter")
+    ap.add_argument("--algos", default=",".join(ALGOS),
+                    help="comma-separated subset of bfs,sssp,cc,pagerank (profiling runs)")
+    ap.add_argument("--no-probe", action="store_true", help="skip the host-link probe")
     return ap.parse_args()
 
 
@@ -211,6 +214,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
+    algos = [a for a in args.algos.split(",") if a]
+    assert all(a in ALGOS for a in algos), args.algos
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -230,11 +235,11 @@ def main():
         params[k] = float(v)
     eng = hytg.Engine(g, budget=int(args.budget_frac * graph_bytes), device=local, params=params)
     eng_s = hytg.Engine(s, budget=int(args.budget_frac * sym_bytes), device=local, params=params)
-    memcpy_gbs, zc_gbs = eng.probe_link(1 << 30, 10)
+    memcpy_gbs, zc_gbs = (float("nan"), float("nan")) if args.no_probe else eng.probe_link(1 << 30, 10)
 
     def one_step(collect):
         per = {}
-        for algo in ALGOS:
+        for algo in algos:
             e = eng_s if algo == "cc" else eng
             src = 0 if algo in ("bfs", "sssp") else None
             t0 = time.perf_counter()
@@ -257,24 +262,27 @@ def main():
     barrier(world)
     clk = clocks.stop()
 
-    edges = sum(p[a]["stats"]["edges_relaxed"] for p in steps for a in ALGOS)
-    dev_ms = sum(p[a]["stats"]["device_ms"] for p in steps for a in ALGOS)
-    wall_ms = sum(p[a]["wall_ms"] for p in steps for a in ALGOS)
-    launches = sum(p[a]["stats"]["kernel_launches"] for p in steps for a in ALGOS)
+    edges = sum(p[a]["stats"]["edges_relaxed"] for p in steps for a in algos)
+    dev_ms = sum(p[a]["stats"]["device_ms"] for p in steps for a in algos)
+    wall_ms = sum(p[a]["wall_ms"] for p in steps for a in algos)
+    launches = sum(p[a]["stats"]["kernel_launches"] for p in steps for a in algos)
     tot_edges, max_ms = aggregate(float(edges), dev_ms, world)
     tot_edges_w, max_wall = aggregate(float(edges), wall_ms, world)
     value = tot_edges / (max_ms * 1e-3) / 1e9
     e2e = tot_edges_w / (max_wall * 1e-3) / 1e9
 
     # host link: bytes moved over the link by the F, C and Z routes / device time
-    link_bytes = sum(sum(p[a]["stats"]["link_bytes"]) for p in steps for a in ALGOS)
+    link_bytes = sum(sum(p[a]["stats"]["link_bytes"]) for p in steps for a in algos)
     link_gbs = link_bytes / (dev_ms * 1e-3) / 1e9
     per_algo = {}
-    for a in ALGOS:
+    for a in algos:
         ed = sum(p[a]["stats"]["edges_relaxed"] for p in steps)
         ms = sum(p[a]["stats"]["device_ms"] for p in steps)
         st = steps[-1][a]["stats"]
+        kk = [sum(p[a]["stats"]["kernel_ms"][i] for p in steps) / len(steps) for i in range(12)]
         per_algo[a] = {"gteps": ed / (ms * 1e-3) / 1e9, "ms": ms / len(steps),
+                       "ms_each_step": [round(p[a]["stats"]["device_ms"], 2) for p in steps],
+                       "kernel_ms": {hytg.KERNEL_KINDS[i]: round(kk[i], 2) for i in range(12) if kk[i]},
                        "iterations": st["iterations"], "edges_relaxed": st["edges_relaxed"],
                        "route_partitions": dict(zip(hytg.ROUTE_NAMES, st["route_partitions"])),
                        "route_edges": dict(zip(hytg.ROUTE_NAMES, st["route_edges"])),
@@ -285,7 +293,7 @@ def main():
     kms = [0.0] * 12
     kcnt = [0] * 12
     for p in steps:
-        for a in ALGOS:
+        for a in algos:
             for i in range(12):
                 kms[i] += p[a]["stats"]["kernel_ms"][i]
                 kcnt[i] += p[a]["stats"]["kernel_count"][i]
@@ -298,7 +306,7 @@ def main():
         r = route_of[dom]
         alg_bytes = 0
         for p in steps:
-            for a in ALGOS:
+            for a in algos:
                 d1 = 8 if a == "sssp" else 4
                 alg_bytes += p[a]["stats"]["route_edges"][r] * d1
         ms = kms[relax[dom]]
@@ -321,14 +329,14 @@ def main():
         cpu = {"value": e_cpu / s_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": sample, "seconds": s_cpu, "host_cores": os.cpu_count()}
 
-    h2d = sum(p[a]["h2d"] for p in steps for a in ALGOS) // len(steps)
-    d2h = sum(p[a]["d2h"] for p in steps for a in ALGOS) // len(steps)
+    h2d = sum(p[a]["h2d"] for p in steps for a in algos) // len(steps)
+    d2h = sum(p[a]["d2h"] for p in steps for a in algos) // len(steps)
     link_per_step = link_bytes // len(steps)
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 (PageRank f32)", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale} bfs+sssp+cc+pagerank, edges in pinned host memory, "
+        "config": {"workload": f"rmat{args.scale} {'+'.join(algos)}, edges in pinned host memory, "
                                f"budget {args.budget_frac:.0%} of graph bytes",
                    "V": g.V, "E": g.E, "E_sym": s.E, "budget_bytes": int(args.budget_frac * graph_bytes),
                    "budget_bytes_cc": int(args.budget_frac * sym_bytes),

@@ -145,7 +145,11 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * (-1 cost model, 1 cache, 2 F, 3 C, 4 Z, 5 random per partition per
  * iteration), "seed" (for force_route 5), "pr_damping", "pr_eps" (FP32
  * residual threshold), "max_iters", "timing" (1: CUDA-event time per kernel
- * kind).  Changing "part_bytes" re-partitions the loaded graph.
+ * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
+ * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),
+ * "hub_replicas" (how many of the first hub ids get per-SM PageRank
+ * accumulators, applied at the next load; default 4096).
+ * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);
 hytg_status hytg_get_param(hytg_ctx *ctx, const char *key, double *value);
@@ -171,6 +175,22 @@ hytg_status hytg_fetch_pagerank_state(hytg_ctx *ctx, float *rank, float *delta, 
 hytg_status hytg_get_stats(hytg_ctx *ctx, hytg_stats *out);
 hytg_status hytg_get_info(hytg_ctx *ctx, hytg_info *out);
 
+/* Hub sorting (Sec. VI-A), a pure host function (no GPU needed): the
+ * floor(frac * V) vertices with the largest H(v) = D_o(v) * D_i(v) (the
+ * paper's normalisation by D_omax * D_imax does not change the order; ties
+ * go to the smaller id) come first in decreasing H, then every other vertex
+ * in increasing id.  offsets: V+1 uint64; dst: offsets[V] uint32 (host).
+ * perm receives V uint32: perm[n] = original id of internal vertex n.
+ * *n_hubs (may be NULL) receives floor(frac * V). */
+hytg_status hytg_hub_order(uint64_t V, const uint64_t *offsets, const uint32_t *dst, double frac,
+                           uint32_t *perm, uint64_t *n_hubs);
+
+/* The internal vertex order of the loaded graph: perm[n] = original id of
+ * internal vertex n (identity when hub sorting is off).  Partitions, the
+ * frontier of hytg_plan_noalloc and the routes refer to internal ids; every
+ * other call takes and returns original ids. */
+hytg_status hytg_get_permutation(hytg_ctx *ctx, uint32_t *perm, uint64_t V);
+
 /* Partition table (Sec. IV): vertex bounds, n_parts + 1 uint64 entries.
  * Partitions start on multiples of 32 vertices; each is the longest run with
  * at most part_edges edges, or a single 32-vertex run if that run alone has
@@ -178,7 +198,8 @@ hytg_status hytg_get_info(hytg_ctx *ctx, hytg_info *out);
 hytg_status hytg_get_partitions(hytg_ctx *ctx, uint64_t *vbounds, uint32_t cap, uint32_t *n_parts);
 
 /* Cost analysis and engine selection alone (Sec. V-A, Alg. 1 cost part) for
- * a caller-given frontier: active (V bytes, nonzero = active) is uploaded,
+ * a caller-given frontier: active (V bytes indexed by original id, nonzero =
+ * active) is uploaded,
  * the count and selection kernels run on the device, and the per-partition
  * results come back: routes[n_parts] (hytg_route), and, if non-NULL,
  * counts[3 * n_parts] = {|A_i|, active edges, 128-byte lines} per partition.
@@ -201,6 +222,8 @@ typedef struct hytg_iter_record {
     uint32_t f_tasks;
     uint64_t route_edges[5];
     uint64_t link_bytes;
+    double device_ms;                 /* CUDA-event time from this iteration's planning to
+                                         the next one's (timing parameter 1), else 0 */
 } hytg_iter_record;
 hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t cap, uint32_t *n);
 

@@ -152,3 +152,36 @@ def combine_tasks(routes: Sequence[int], k: int = PAPER_K,
     if cur:
         groups.append(cur)
     return groups, vc, vz, vcache
+
+
+def hub_order(off: np.ndarray, dst: np.ndarray, frac: float = 0.08) -> List[int]:
+    """Sec. VI-A hub sorting: the floor(frac * V) vertices with the largest
+    H(v) = D_o(v) D_i(v) / (D_omax D_imax) first, in decreasing H (ties: smaller
+    id first), then all other vertices in their natural order.  Returns perm
+    with perm[new] = original id.  The normalising constant is positive and
+    common to all vertices, so the order uses D_o(v) D_i(v) in exact integers."""
+    V = len(off) - 1
+    d_out = [int(off[v + 1]) - int(off[v]) for v in range(V)]
+    d_in = [0] * V
+    for x in dst.tolist():
+        d_in[x] += 1
+    k = int(frac * V)
+    ranked = sorted(range(V), key=lambda v: (-(d_out[v] * d_in[v]), v))
+    hubs = ranked[:k]
+    chosen = set(hubs)
+    return hubs + [v for v in range(V) if v not in chosen]
+
+
+def relabel(off: np.ndarray, dst: np.ndarray, w, perm):
+    """The CSR in the order perm (perm[new] = old): row new is old row perm[new]
+    with every destination renamed to its new id."""
+    V = len(off) - 1
+    inv = np.empty(V, np.int64)
+    inv[np.asarray(perm, np.int64)] = np.arange(V)
+    deg = np.diff(off.astype(np.int64))[np.asarray(perm, np.int64)]
+    off2 = np.concatenate([[0], np.cumsum(deg)]).astype(np.uint64)
+    rows = [np.arange(int(off[o]), int(off[o + 1])) for o in perm]
+    idx = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    dst2 = inv[dst.astype(np.int64)[idx]].astype(np.uint32)
+    w2 = None if w is None else w[idx]
+    return off2, dst2, w2

@@ -130,7 +130,13 @@ struct AlgoState {
     unsigned int *bm_cur, *bm_next;
     unsigned int *overflow;  // device flag
     unsigned int n_arrays;   // edge arrays read per edge (1 or 2)
+    const unsigned int *perm;// internal id -> original id (hub sorting), or nullptr
+    // PageRank pushes to hub ids [0, n_hub_rep) go to per-SM replicas
+    // hub_rep[(smid % kHubReplicas) * n_hub_rep + v], summed into delta once per iteration
+    float *hub_rep;
+    unsigned int n_hub_rep;
 };
+constexpr unsigned int kHubReplicas = 256;
 
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
                          const SegArrays &sa, unsigned long long m, cudaStream_t s);
@@ -165,6 +171,11 @@ cudaError_t launch_init(const AlgoState &st, unsigned long long V, unsigned long
                         unsigned int source, cudaStream_t s);
 cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float *out,
                                double *sums, cudaStream_t s);
+cudaError_t launch_pr_frontier(const AlgoState &st, unsigned long long V,
+                               unsigned long long n_words_alloc, cudaStream_t s);
+cudaError_t launch_hub_reduce(const AlgoState &st, cudaStream_t s);
+cudaError_t launch_to_original(const unsigned int *perm, const unsigned int *in, float *out,
+                               unsigned long long V, cudaStream_t s);
 cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *bm,
                                  unsigned long long V, unsigned long long n_words_alloc,
                                  cudaStream_t s);

@@ -73,7 +73,14 @@ struct hytg_ctx {
     bool weighted = false;
     uint32_t *h_dst = nullptr, *h_w = nullptr;          // pinned, mapped
     const uint32_t *m_dst = nullptr, *m_w = nullptr;    // device view of the same memory
-    std::vector<uint64_t> h_off;
+    std::vector<uint64_t> h_off;                         // row offsets in internal ids
+    // hub sorting (Sec. VI-A): internal id n holds original vertex perm[n]
+    bool permuted = false;
+    uint64_t n_hubs = 0;
+    std::vector<uint32_t> h_perm, h_inv;                 // internal->original, original->internal
+    unsigned int *d_perm = nullptr;
+    float *d_hub_rep = nullptr;                          // kHubReplicas x n_hub_rep floats
+    unsigned int n_hub_rep = 0;
 
     // partitions
     uint64_t part_edges = 0, max_part_edges = 0;
@@ -113,9 +120,11 @@ struct hytg_ctx {
     // parameters
     double alpha = 0.8, beta = 0.4, gamma = 0.625, m = 128, MR = 256, k = 4;
     double part_bytes = 4.0 * 1024 * 1024;
-    double streams = 4, staging_frac = 0.5, compact_frac = 0.25;
+    double streams = 4, staging_frac = 0.5, compact_frac = 0.05;
     double force_route = -1, seed = 1, pr_damping = 0.85, pr_eps = 1e-9, max_iters = 1e8;
     double timing = 0;
+    double hub_frac = 0.08;                              // Sec. VI-A: top 8 % of vertices
+    double hub_replicas = 4096;                          // hub ids with per-SM accumulators
 
     // last run
     bool have_result = false;
@@ -123,6 +132,7 @@ struct hytg_ctx {
     hytg_stats stats{};
     std::vector<hytg_iter_record> iters;
     std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> iter_ev;                    // per-iteration marks (timing on)
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
 };
@@ -158,7 +168,13 @@ void free_graph(hytg_ctx *c) {
     c->m_dst = c->m_w = nullptr;
     dfree(c->d_off); dfree(c->d_val); dfree(c->d_delta); dfree(c->d_bm[0]); dfree(c->d_bm[1]);
     dfree(c->d_out); dfree(c->d_ebase); dfree(c->d_soff); dfree(c->d_pay); dfree(c->d_tiles);
-    dfree(c->d_seg); dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf);
+    dfree(c->d_seg); dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm);
+    dfree(c->d_hub_rep);
+    c->n_hub_rep = 0;
+    c->permuted = false;
+    c->n_hubs = 0;
+    c->h_perm.clear();
+    c->h_inv.clear();
     for (int i = 0; i < 2; ++i) {
         if (c->h_sumbuf[i]) cudaFreeHost(c->h_sumbuf[i]);
         c->h_sumbuf[i] = nullptr;
@@ -428,6 +444,10 @@ AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
     st.bm_next = c->d_bm[cur ^ 1];
     st.overflow = c->d_overflow;
     st.n_arrays = (algo == kSSSP) ? 2 : 1;
+    st.perm = c->d_perm;
+    const bool pr = (algo == kPR || algo == kPPR);
+    st.hub_rep = pr ? c->d_hub_rep : nullptr;
+    st.n_hub_rep = pr && c->d_hub_rep ? c->n_hub_rep : 0;
     return st;
 }
 
@@ -435,6 +455,11 @@ AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
 // copy (-> ev_sum[buf]), binning (-> ev_bin), and the device-sized cache and
 // zero-copy relaxes.
 hytg_status issue_plan(hytg_ctx *c, int algo, int cur, uint32_t it, int buf, bool with_work) {
+    if (c->timing != 0 && with_work) {
+        cudaEvent_t e = pool_event(c);
+        CK(cudaEventRecord(e, c->s_main));
+        c->iter_ev.push_back(e);
+    }
     GraphDev g = graph_dev(c);
     AlgoState st = algo_state(c, algo, cur);
     PartArrays pa = part_arrays(c);
@@ -442,6 +467,11 @@ hytg_status issue_plan(hytg_ctx *c, int algo, int cur, uint32_t it, int buf, boo
     ListArrays la = list_arrays(c);
     Summary *sum = (Summary *)c->d_sumbuf;
     const uint32_t N = g.N;
+    if ((algo == kPR || algo == kPPR) && it > 0) {
+        ScopedTime t(c, HYTG_K_OTHER, c->s_main);
+        CK(launch_hub_reduce(st, c->s_main));
+        CK(launch_pr_frontier(st, c->V, c->n_words_alloc, c->s_main));
+    }
     CK(cudaMemsetAsync(pa.n_act, 0, (size_t)N * 8 * 4, c->s_main));
     { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_count(g, st, pa, sa, (unsigned long long)c->m, c->s_main)); }
     { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_select(g, pa, sa, cost_params(c, algo, it), sum, c->s_main)); }
@@ -587,10 +617,37 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
                 return fail(c, HYTG_ERR_HOSTMEM, "cudaHostAlloc of the weight array failed");
             }
         }
-        parallel_chunks(E, [&](uint64_t lo, uint64_t hi) {
-            memcpy(c->h_dst + lo, dst + lo, (hi - lo) * 4);
-            if (weights) memcpy(c->h_w + lo, weights + lo, (hi - lo) * 4);
-        });
+        if (c->hub_frac > 0.0) {
+            // hub sorting: relabel so that the hubs are internal ids [0, n_hubs)
+            c->h_perm.resize(V);
+            uint64_t nh = 0;
+            hytg_status hs = hytg_hub_order(V, offsets, dst, c->hub_frac, c->h_perm.data(), &nh);
+            if (hs != HYTG_OK) { free_graph(c); return fail(c, hs, "hub ordering failed"); }
+            c->h_inv.resize(V);
+            for (uint64_t n = 0; n < V; ++n) c->h_inv[c->h_perm[n]] = (uint32_t)n;
+            c->h_off.assign(V + 1, 0);
+            for (uint64_t n = 0; n < V; ++n) {
+                const uint64_t o = c->h_perm[n];
+                c->h_off[n + 1] = c->h_off[n] + (offsets[o + 1] - offsets[o]);
+            }
+            const uint32_t *inv = c->h_inv.data();
+            parallel_chunks(V, [&](uint64_t lo, uint64_t hi) {
+                for (uint64_t n = lo; n < hi; ++n) {
+                    const uint64_t o = c->h_perm[n], s0 = offsets[o], len = offsets[o + 1] - s0;
+                    uint32_t *d = c->h_dst + c->h_off[n];
+                    for (uint64_t j = 0; j < len; ++j) d[j] = inv[dst[s0 + j]];
+                    if (weights) memcpy(c->h_w + c->h_off[n], weights + s0, len * 4);
+                }
+            });
+            c->permuted = true;
+            c->n_hubs = nh;
+        } else {
+            parallel_chunks(E, [&](uint64_t lo, uint64_t hi) {
+                memcpy(c->h_dst + lo, dst + lo, (hi - lo) * 4);
+                if (weights) memcpy(c->h_w + lo, weights + lo, (hi - lo) * 4);
+            });
+            c->h_off.assign(offsets, offsets + V + 1);
+        }
         void *mp = nullptr;
         CK(cudaHostGetDevicePointer(&mp, c->h_dst, 0));
         c->m_dst = (const uint32_t *)mp;
@@ -601,13 +658,21 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         c->V = V;
         c->E = E;
         c->weighted = weights != nullptr;
-        c->h_off.assign(offsets, offsets + V + 1);
         c->part_edges = std::max<uint64_t>(1, (uint64_t)(c->part_bytes / 4));
         make_partitions(c);
         c->n_segs = (V + kSegVerts - 1) / kSegVerts;
         c->n_words_alloc = c->n_segs * kSegWords;
         CK(cudaMalloc(&c->d_off, (V + 1) * 8));
-        CK(cudaMemcpy(c->d_off, offsets, (V + 1) * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_off, c->h_off.data(), (V + 1) * 8, cudaMemcpyHostToDevice));
+        if (c->permuted) {
+            CK(cudaMalloc(&c->d_perm, V * 4));
+            CK(cudaMemcpy(c->d_perm, c->h_perm.data(), V * 4, cudaMemcpyHostToDevice));
+            c->n_hub_rep = (unsigned int)std::min<uint64_t>(c->n_hubs, (uint64_t)c->hub_replicas);
+            if (c->n_hub_rep) {
+                CK(cudaMalloc(&c->d_hub_rep, (size_t)kHubReplicas * c->n_hub_rep * 4));
+                CK(cudaMemset(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4));
+            }
+        }
         CK(cudaMalloc(&c->d_val, V * 4));
         CK(cudaMalloc(&c->d_delta, V * 4));
         CK(cudaMalloc(&c->d_out, V * 4));
@@ -684,6 +749,8 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "pr_eps") { if (v <= 0) return bad(); c->pr_eps = v; }
     else if (k == "max_iters") { if (v < 1) return bad(); c->max_iters = v; }
     else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
+    else if (k == "hub_frac") { if (v < 0 || v > 1) return bad(); c->hub_frac = v; }
+    else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -707,6 +774,8 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "pr_eps") *v = c->pr_eps;
     else if (k == "max_iters") *v = c->max_iters;
     else if (k == "timing") *v = c->timing;
+    else if (k == "hub_frac") *v = c->hub_frac;
+    else if (k == "hub_replicas") *v = c->hub_replicas;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -724,6 +793,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             return fail(c, HYTG_ERR_ARG, "this algorithm takes exactly one source");
         source = sources[0];
         if (source >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
+        if (c->permuted) source = c->h_inv[source];
     }
     if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
     try {
@@ -733,6 +803,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats = hytg_stats{};
         c->iters.clear();
         c->timed.clear();
+        c->iter_ev.clear();
         c->ev_used = 0;
         const int n_arrays = (algo == kSSSP) ? 2 : 1;
         CK(cudaEventRecord(c->ev_run[0], c->s_main));
@@ -743,6 +814,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         Carve &cv = c->carve;
         int cur = 0;
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
+        if ((algo == kPR || algo == kPPR) && c->d_hub_rep)
+            CK(cudaMemsetAsync(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4, c->s_main));
         {
             AlgoState st = algo_state(c, algo, cur);
             ScopedTime t(c, HYTG_K_INIT, c->s_main);
@@ -787,16 +860,18 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 }
                 const uint32_t slot = n_tasks % cv.n_slots;
                 cudaStream_t fs = c->s_f[slot];
-                if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
-                    f_streams_used.push_back((int)slot);
-                    CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
-                }
                 const uint64_t e0 = c->part_eb[i];
                 {
+                    // the copy needs only the route decision (already on the host)
+                    // and the slot's previous relax (same stream), not the lists
                     ScopedTime t(c, HYTG_K_COPY_F, fs);
                     CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, fs));
                     if (n_arrays == 2)
                         CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+                }
+                if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
+                    f_streams_used.push_back((int)slot);
+                    CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
                 }
                 RelaxTask t{};
                 t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
@@ -875,10 +950,13 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         }
         c->stats.iterations = it;
         // finalisation
-        if (algo == kPR || algo == kPPR) {
+        {
             AlgoState st = algo_state(c, algo, cur);
             ScopedTime t(c, HYTG_K_FINAL, c->s_main);
-            CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
+            if (algo == kPR || algo == kPPR)
+                CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
+            else
+                CK(launch_to_original(st.perm, c->d_val, c->d_out, c->V, c->s_main));
         }
         unsigned int ovf = 0, ierr = 0;
         double prs[2] = {0, 0};
@@ -898,6 +976,11 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats.wall_ms = std::chrono::duration<double, std::milli>(t_end - t_start).count();
         c->stats.pr_rank_sum = prs[0];
         c->stats.pr_residual_sum = prs[1];
+        for (size_t i = 0; i + 1 < c->iter_ev.size() && i < c->iters.size(); ++i) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, c->iter_ev[i], c->iter_ev[i + 1]) == cudaSuccess)
+                c->iters[i].device_ms = ms;
+        }
         for (auto &tl : c->timed) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, tl.a, tl.b) == cudaSuccess) {
@@ -928,8 +1011,7 @@ hytg_status hytg_fetch_result(hytg_ctx *c, void *out, uint64_t out_bytes) {
     if (!c->have_result) return fail(c, HYTG_ERR_STATE, "no completed run");
     if (out_bytes < c->V * 4) return fail(c, HYTG_ERR_ARG, "output buffer too small");
     CK(cudaSetDevice(c->device));
-    const void *src = (c->last_algo == kPR || c->last_algo == kPPR) ? (const void *)c->d_out : (const void *)c->d_val;
-    CK(cudaMemcpyAsync(out, src, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaMemcpyAsync(out, c->d_out, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
     CK(cudaStreamSynchronize(c->s_main));
     return HYTG_OK;
 }
@@ -940,8 +1022,19 @@ hytg_status hytg_fetch_pagerank_state(hytg_ctx *c, float *rank, float *delta, ui
         return fail(c, HYTG_ERR_STATE, "no completed PageRank run");
     if (V < c->V) return fail(c, HYTG_ERR_ARG, "buffers too small");
     CK(cudaSetDevice(c->device));
-    if (rank) CK(cudaMemcpyAsync(rank, c->d_val, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
-    if (delta) CK(cudaMemcpyAsync(delta, c->d_delta, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    // original vertex order; d_out (the normalised result) is rebuilt afterwards
+    if (rank) {
+        CK(launch_to_original(c->d_perm, c->d_val, c->d_out, c->V, c->s_main));
+        CK(cudaMemcpyAsync(rank, c->d_out, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    }
+    if (delta) {
+        CK(launch_to_original(c->d_perm, (const unsigned int *)c->d_delta, c->d_out, c->V, c->s_main));
+        CK(cudaMemcpyAsync(delta, c->d_out, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    }
+    {
+        AlgoState st = algo_state(c, c->last_algo, 0);
+        CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
+    }
     CK(cudaStreamSynchronize(c->s_main));
     return HYTG_OK;
 }
@@ -996,9 +1089,15 @@ hytg_status hytg_plan(hytg_ctx *c, hytg_algo algo_in, const uint8_t *active, uin
     CK(cudaSetDevice(c->device));
     hytg_status s = plan_carve(c, algo == kSSSP ? 2 : 1);
     if (s != HYTG_OK) return s;
+    std::vector<uint8_t> act_int;
+    if (c->permuted) {
+        act_int.resize(c->V);
+        for (uint64_t n = 0; n < c->V; ++n) act_int[n] = active[c->h_perm[n]];
+        active = act_int.data();
+    }
     unsigned char *d_act = nullptr;
     CK(cudaMalloc(&d_act, c->V));
-    cudaError_t e = cudaMemcpyAsync(d_act, active, c->V, cudaMemcpyHostToDevice, c->s_main);
+    cudaError_t e = cudaMemcpy(d_act, active, c->V, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_upload_bitmap(d_act, c->d_bm[0], c->V, c->n_words_alloc, c->s_main);
     if (e != cudaSuccess) { cudaFree(d_act); return fail(c, HYTG_ERR_CUDA, cudaGetErrorString(e)); }
     c->have_result = false;
@@ -1076,6 +1175,14 @@ hytg_status hytg_probe_link(hytg_ctx *c, uint64_t bytes, uint32_t reps, double *
     if (sink) cudaFree(sink);
     cudaFreeHost(h);
     return st;
+}
+
+hytg_status hytg_get_permutation(hytg_ctx *c, uint32_t *perm, uint64_t V) {
+    if (!c || !perm) return HYTG_ERR_ARG;
+    if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
+    if (V < c->V) return fail(c, HYTG_ERR_ARG, "buffer too small");
+    for (uint64_t n = 0; n < c->V; ++n) perm[n] = c->permuted ? c->h_perm[n] : (uint32_t)n;
+    return HYTG_OK;
 }
 
 hytg_status hytg_get_iterations(hytg_ctx *c, hytg_iter_record *out, uint32_t cap, uint32_t *n) {

@@ -17,7 +17,7 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
         switch (st.algo) {
             case kBFS:
             case kSSSP: st.val[v] = (v == source) ? 0u : 0xFFFFFFFFu; break;
-            case kCC: st.val[v] = (unsigned int)v; break;
+            case kCC: st.val[v] = st.perm ? st.perm[v] : (unsigned int)v; break;  // original id
             case kPR: st.rank[v] = 0.0f; st.delta[v] = base; break;
             default: st.rank[v] = 0.0f; st.delta[v] = (v == source) ? base : 0.0f; break;
         }
@@ -36,6 +36,35 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
         st.bm_next[w] = 0u;
     }
     if (t0 == 0) *st.overflow = 0u;
+}
+
+// Delta-PageRank frontier: v is active iff delta[v] > eps (Sec. VI-A, with
+// the threshold reading of the design notes).  Inactive vertices always hold
+// delta <= eps, so this equals "delta crossed eps during the iteration".
+__global__ void k_pr_frontier(AlgoState st, unsigned long long V, unsigned long long n_words_alloc) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long base = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull;
+         base < n_words_alloc * 32; base += stride) {
+        const unsigned long long v = base + lane;
+        const bool act = v < V && st.delta[v] > st.eps;
+        const unsigned int bits = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) st.bm_cur[base >> 5] = bits;
+    }
+}
+
+// Fold the per-SM hub replicas into delta and clear them.
+__global__ void k_hub_reduce(AlgoState st) {
+    const unsigned int K = st.n_hub_rep;
+    for (unsigned int v = blockIdx.x * blockDim.x + threadIdx.x; v < K; v += gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (unsigned int r = 0; r < kHubReplicas; ++r) {
+            float *p = st.hub_rep + (size_t)r * K + v;
+            s += *p;
+            *p = 0.0f;
+        }
+        st.delta[v] += s;
+    }
 }
 
 __global__ void k_pr_sums(AlgoState st, unsigned long long V, double *sums) {
@@ -74,7 +103,16 @@ __global__ void k_pr_normalise(AlgoState st, unsigned long long V, const double 
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
          v += stride)
-        out[v] = (float)((double)st.rank[v] * inv);
+        out[st.perm ? st.perm[v] : v] = (float)((double)st.rank[v] * inv);
+}
+
+// Copy a per-vertex array from internal to original vertex order.
+__global__ void k_to_original(const unsigned int *perm, const unsigned int *in, unsigned int *out,
+                              unsigned long long V) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += stride)
+        out[perm ? perm[v] : v] = in[v];
 }
 
 __global__ void k_upload_bitmap(const unsigned char *active, unsigned int *bm, unsigned long long V,
@@ -125,6 +163,27 @@ cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float 
     if (e != cudaSuccess) return e;
     k_pr_sums<<<grid_for(V, 256), 256, 0, s>>>(st, V, sums);
     k_pr_normalise<<<grid_for(V, 256), 256, 0, s>>>(st, V, sums, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_reduce(const AlgoState &st, cudaStream_t s) {
+    if (!st.hub_rep || st.n_hub_rep == 0) return cudaSuccess;
+    k_hub_reduce<<<(st.n_hub_rep + 255) / 256, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pr_frontier(const AlgoState &st, unsigned long long V,
+                               unsigned long long n_words_alloc, cudaStream_t s) {
+    const unsigned long long n = n_words_alloc * 32;
+    unsigned long long g = (n + 255) / 256;
+    if (g > 152ull * 16) g = 152ull * 16;
+    k_pr_frontier<<<(unsigned int)g, 256, 0, s>>>(st, V, n_words_alloc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_original(const unsigned int *perm, const unsigned int *in, float *out,
+                               unsigned long long V, cudaStream_t s) {
+    k_to_original<<<grid_for(V, 256), 256, 0, s>>>(perm, in, (unsigned int *)out, V);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,8 @@ namespace hytg {
 
 namespace {
 
+constexpr int kBatch = 4;   // bitmap words whose loads are issued together
+
 // Partition holding bitmap word `widx` (bounds are word indices).
 __device__ __forceinline__ unsigned int find_part(const unsigned int *wb, unsigned int N,
                                                   unsigned long long widx) {
@@ -43,10 +45,33 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
             const unsigned int bits = st.bm_cur[wbase + lane];
             unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
             while (nz) {
-                const int src = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const unsigned int w = __shfl_sync(0xffffffffu, bits, src);
-                const unsigned long long widx = wbase + src;
+                unsigned int wq[kBatch];
+                unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    wq[q] = 0;
+                    wi[q] = 0;
+                    if (nz) {                      // warp-uniform
+                        const int src = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        wq[q] = __shfl_sync(0xffffffffu, bits, src);
+                        wi[q] = wbase + src;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    o0[q] = o1[q] = 0;
+                    if ((wq[q] >> lane) & 1u) {
+                        const unsigned long long v = wi[q] * 32 + lane;
+                        o0[q] = g.off[v];
+                        o1[q] = g.off[v + 1];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                if (wq[q] == 0) continue;          // warp-uniform
+                const unsigned int w = wq[q];
+                const unsigned long long widx = wi[q];
                 if (widx < p_lo || widx >= p_hi) {
                     if (cur_p != 0xFFFFFFFFu && lane == 0 && a_nact) {
                         atomicAdd(&pa.n_act[cur_p], a_nact);
@@ -59,14 +84,9 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
                 }
-                const bool active = (w >> lane) & 1u;
-                unsigned long long deg = 0, ln = 0;
-                if (active) {
-                    const unsigned long long v = widx * 32 + lane;
-                    const unsigned long long o0 = g.off[v], o1 = g.off[v + 1];
-                    deg = o1 - o0;
-                    ln = (unsigned long long)st.n_arrays * lines_spanned(o0 * elem, deg * elem, m);
-                }
+                const unsigned long long deg = o1[q] - o0[q];
+                const unsigned long long ln =
+                    (unsigned long long)st.n_arrays * lines_spanned(o0[q] * elem, deg * elem, m);
                 const unsigned int ent = __popc(__ballot_sync(0xffffffffu, deg > 0));
                 const unsigned long long e_sum = warp_sum_u64(deg);
                 const unsigned long long l_sum = warp_sum_u64(ln);
@@ -76,6 +96,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                 a_lines += l_sum;
                 seg_ent += ent;
                 seg_edges += e_sum;
+                }
             }
         }
         if (lane == 0) {
@@ -229,10 +250,41 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
             if (bits) st.bm_cur[wbase + lane] = 0u;
             unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
             while (nz) {
-                const int src = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const unsigned int w = __shfl_sync(0xffffffffu, bits, src);
-                const unsigned long long widx = wbase + src;
+                // up to kBatch nonzero words at once: their loads are issued
+                // together before the per-word scans (latency hiding)
+                unsigned int wq[kBatch];
+                unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
+                unsigned int vv[kBatch];
+                float rk[kBatch];
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    wq[q] = 0;
+                    wi[q] = 0;
+                    if (nz) {                      // warp-uniform
+                        const int src = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        wq[q] = __shfl_sync(0xffffffffu, bits, src);
+                        wi[q] = wbase + src;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    o0[q] = o1[q] = 0;
+                    vv[q] = 0;
+                    rk[q] = 0.0f;
+                    if ((wq[q] >> lane) & 1u) {
+                        const unsigned long long v = wi[q] * 32 + lane;
+                        o0[q] = g.off[v];
+                        o1[q] = g.off[v + 1];
+                        if (is_pr) { vv[q] = __float_as_uint(st.delta[v]); rk[q] = st.rank[v]; }
+                        else vv[q] = st.val[v];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                if (wq[q] == 0) continue;          // warp-uniform
+                const unsigned int w = wq[q];
+                const unsigned long long widx = wi[q];
                 if (widx < p_lo || widx >= p_hi) {
                     cur_p = find_part(g.part_wb, g.N, widx);
                     p_lo = g.part_wb[cur_p];
@@ -245,19 +297,17 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                 }
                 const bool active = (w >> lane) & 1u;
                 const unsigned long long v = widx * 32 + lane;
-                unsigned long long o0 = 0, deg = 0;
+                const unsigned long long deg = o1[q] - o0[q];
                 unsigned int pay = 0;
                 if (active) {
-                    o0 = g.off[v];
-                    deg = g.off[v + 1] - o0;
                     if (is_pr) {
                         // take the accumulated delta (Sec. VI-A delta-based PageRank)
-                        const float dl = st.delta[v];
+                        const float dl = __uint_as_float(vv[q]);
                         st.delta[v] = 0.0f;
-                        st.rank[v] += dl;
+                        st.rank[v] = rk[q] + dl;
                         pay = __float_as_uint(deg ? st.damping * dl / (float)deg : 0.0f);
                     } else {
-                        pay = st.val[v];
+                        pay = vv[q];
                     }
                 }
                 const bool is_ent = deg > 0;
@@ -272,7 +322,7 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                         atomicOr(la.err, 2u);
                     } else {
                         la.ebase[idx] = eb;
-                        la.soff[idx] = o0;
+                        la.soff[idx] = o0[q];
                         la.pay[idx] = pay;
                         const unsigned int rel = (unsigned int)(idx - rbase);
                         for (unsigned long long t = t0; t <= t1; ++t) la.tile_first[tbase + t] = rel;
@@ -280,6 +330,7 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                 }
                 run_ent += __popc(bal);
                 run_edg += __shfl_sync(0xffffffffu, incl, 31);
+                }
             }
         }
     }

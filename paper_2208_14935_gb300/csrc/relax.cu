@@ -108,13 +108,24 @@ __device__ __forceinline__ int tile_setup(TileSmem &sm, const ListArrays &la, co
     return n_slots;
 }
 
+__device__ __forceinline__ unsigned int sm_id() {
+    unsigned int id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
+// hub_rep: this SM's replica row of the hub accumulators (PageRank only).
 template <int ALGO>
 __device__ __forceinline__ void relax_edge(const AlgoState &st, unsigned int v, unsigned int pay,
-                                           unsigned int w) {
+                                           unsigned int w, float *hub_rep) {
     if (ALGO == kPR || ALGO == kPPR) {
-        const float msg = __uint_as_float(pay);
-        const float old = atomicAdd(&st.delta[v], msg);
-        if (old <= st.eps && old + msg > st.eps) atomicOr(&st.bm_next[v >> 5], 1u << (v & 31));
+        // fire-and-forget reduction; the next frontier is rebuilt from delta
+        // (delta > eps) by k_pr_frontier once every relax of the iteration is
+        // done.  Pushes to the hottest vertices (hub-sorted ids below
+        // n_hub_rep) go to this SM's replica, so thousands of SMs' updates do
+        // not serialise on one L2 address.
+        if (v < st.n_hub_rep) atomicAdd(&hub_rep[v], __uint_as_float(pay));
+        else atomicAdd(&st.delta[v], __uint_as_float(pay));
     } else {
         unsigned int nv;
         if (ALGO == kBFS) {
@@ -126,9 +137,13 @@ __device__ __forceinline__ void relax_edge(const AlgoState &st, unsigned int v, 
         } else {
             nv = pay;
         }
+        // Fire-and-forget min and frontier bit when the pushed value beats the
+        // value seen now.  If a concurrent push lowered v further in between,
+        // v is still marked active: it then re-pushes its (current) value
+        // next iteration, which is redundant but never wrong for min-updates.
         if (nv < __ldcg(&st.val[v])) {
-            const unsigned int old = atomicMin(&st.val[v], nv);
-            if (nv < old) atomicOr(&st.bm_next[v >> 5], 1u << (v & 31));
+            atomicMin(&st.val[v], nv);
+            atomicOr(&st.bm_next[v >> 5], 1u << (v & 31));
         }
     }
 }
@@ -142,6 +157,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
     const bool weighted = (ALGO == kSSSP);
+    float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
         const int n = tile_setup(sm, la, sum, t, tile, kb, ke, &k0);
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
         }
 #pragma unroll
         for (int j = 0; j < kRelaxIPT; ++j)
-            if (dv[j] != kInf) relax_edge<ALGO>(st, dv[j], pv[j], wv[j]);
+            if (dv[j] != kInf) relax_edge<ALGO>(st, dv[j], pv[j], wv[j], hub_rep);
         __syncthreads();
     }
 }

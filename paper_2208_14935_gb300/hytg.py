@@ -49,7 +49,8 @@ class hytg_info(ctypes.Structure):
 
 class hytg_iter_record(ctypes.Structure):
     _fields_ = [("active_vertices", u64), ("active_edges", u64), ("route_partitions", u32 * 5),
-                ("f_tasks", u32), ("route_edges", u64 * 5), ("link_bytes", u64)]
+                ("f_tasks", u32), ("route_edges", u64 * 5), ("link_bytes", u64),
+                ("device_ms", dbl)]
 
 
 class hytg_cost_params(ctypes.Structure):
@@ -93,6 +94,8 @@ def load(path: Optional[str] = None):
             "hytg_plan": [vp, i32, vp, vp, vp, u32],
             "hytg_probe_link": [vp, u64, u32, P(dbl), P(dbl)],
             "hytg_get_iterations": [vp, vp, u32, P(u32)],
+            "hytg_hub_order": [u64, vp, vp, dbl, vp, P(u64)],
+            "hytg_get_permutation": [vp, vp, u64],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -218,6 +221,23 @@ def hytg_plan_noalloc(algo: int, frontier_ptr: int, offsets_ptr: int, V: int, vb
                                     vp(routes_ptr), vp(counts_ptr), vp(stream) if stream else None)
 
 
+def hytg_hub_order(g, frac: float = 0.08):
+    """Hub-sorting order (pure host): perm[n] = original id of internal vertex n."""
+    off = np.ascontiguousarray(g.off, np.uint64)
+    dst = np.ascontiguousarray(g.dst, np.uint32)
+    perm = np.empty(g.V, np.uint32)
+    nh = u64()
+    _check(None, load().hytg_hub_order(g.V, _ptr(off), _ptr(dst), float(frac), _ptr(perm),
+                                       ctypes.byref(nh)))
+    return perm, nh.value
+
+
+def hytg_get_permutation(ctx, V: int) -> np.ndarray:
+    perm = np.empty(V, np.uint32)
+    _check(ctx, load().hytg_get_permutation(ctx, _ptr(perm), V))
+    return perm
+
+
 def hytg_probe_link(ctx, nbytes: int = 1 << 30, reps: int = 10):
     a, b = dbl(), dbl()
     _check(ctx, load().hytg_probe_link(ctx, int(nbytes), reps, ctypes.byref(a), ctypes.byref(b)))
@@ -299,6 +319,9 @@ class Engine:
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
         n = self.info()["n_parts"]
         return hytg_plan(self.ctx, a, active, n)
+
+    def permutation(self) -> np.ndarray:
+        return hytg_get_permutation(self.ctx, self.V)
 
     def iterations(self):
         return hytg_get_iterations(self.ctx)

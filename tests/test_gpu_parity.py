@@ -172,10 +172,20 @@ def test_mesh_high_diameter(hy):
     e.close()
 
 
-def test_partition_table_matches_oracle(hy, rmat16):
+def internal_graph(e, g):
+    """The graph in the engine's internal (hub-sorted) vertex order, built by the oracle."""
+    perm = e.permutation()
+    assert perm.tolist() == pl.hub_order(g.off, g.dst, e.get_param("hub_frac"))
+    off2, dst2, w2 = pl.relabel(g.off, g.dst, g.w, perm.tolist())
+    return gg.CSR(g.V, g.E, off2, dst2, w2), perm
+
+
+@pytest.mark.parametrize("hub_frac", [0.0, 0.08])
+def test_partition_table_matches_oracle(hy, rmat16, hub_frac):
     for pb in (4096, 64 * 1024, 1 << 20, 4 << 20):
-        e = engine(hy, rmat16, 1 << 24, part_bytes=pb)
-        assert e.partitions().tolist() == pl.partition_bounds(rmat16.off, pb // 4)
+        e = engine(hy, rmat16, 1 << 24, part_bytes=pb, hub_frac=hub_frac)
+        g2, _ = internal_graph(e, rmat16)
+        assert e.partitions().tolist() == pl.partition_bounds(g2.off, pb // 4)
         e.close()
 
 
@@ -186,20 +196,30 @@ def test_planner_matches_oracle(hy, rmat16, algo):
     params = dict(alpha=0.8, beta=0.4, gamma=0.625, MR=8)
     e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, **params)
     vb = e.partitions()
-    E_part = np.diff(rmat16.off[vb.astype(np.int64)].astype(np.int64))
+    g2, perm = internal_graph(e, rmat16)
+    E_part = np.diff(g2.off[vb.astype(np.int64)].astype(np.int64))
     rng = np.random.default_rng(5)
     d1 = 8 if algo == "sssp" else 4
     n_arrays = 2 if algo == "sssp" else 1
     for dens in (1e-4, 1e-3, 0.01, 0.1, 0.5, 1.0):
         act = (rng.random(rmat16.V) < dens).astype(np.uint8)
         routes, counts = e.plan(algo, act)
-        na, ae, ln = orc.partition_counts(rmat16, act, vb, 4, n_arrays, 128)
+        na, ae, ln = orc.partition_counts(g2, act[perm], vb, 4, n_arrays, 128)
         assert np.array_equal(counts[:, 0], na) and np.array_equal(counts[:, 1], ae)
         assert np.array_equal(counts[:, 2], ln)
         n_cached = e.info()["n_cached"]
         want = pl.plan(E_part, na, ae, ln, d1, resident=range(n_cached), m=128, MR=8,
                        alpha=Fraction("0.8"), beta=Fraction("0.4"), gamma=Fraction("0.625"))
         assert routes.tolist() == want, dens
+    e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "cc", "pagerank"])
+def test_without_hub_sorting(hy, rmat16, rmat16_sym, algo):
+    g = rmat16_sym if algo == "cc" else rmat16
+    e = engine(hy, g, edge_bytes(g, algo) // 4, hub_frac=0.0)
+    assert e.permutation().tolist() == list(range(g.V))
+    check(g, algo, e.run(algo, 0 if algo in ("bfs", "sssp") else None))
     e.close()
 
 

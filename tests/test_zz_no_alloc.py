@@ -22,7 +22,7 @@ def test_plan_noalloc_matches_plan():
     hytg.load()
     g = gg.rmat(16, seed=1)
     params = dict(alpha=0.8, beta=0.4, gamma=0.625, MR=8)
-    e = hytg.Engine(params={"part_bytes": 64 * 1024, **params})
+    e = hytg.Engine(params={"part_bytes": 64 * 1024, "hub_frac": 0.0, **params})
     e.load(g)
     e.set_budget(g.E * 8 // 4)
     vb = e.partitions()
