@@ -10,10 +10,11 @@ namespace hytg {
 constexpr int kRoutes = 5;            // NONE, CACHE, F, C, Z (hytg_route)
 constexpr int kRouteNone = 0, kRouteCache = 1, kRouteF = 2, kRouteC = 3, kRouteZ = 4;
 
-// Frontier bitmap: one bit per vertex, 32-bit words; kernels walk it in
-// segments of 128 words (4096 vertices), one warp per segment.
-constexpr int kSegWords = 128;
-constexpr int kSegVerts = kSegWords * 32;
+// Frontier bitmap: one bit per vertex, 32-bit words, padded to a multiple of
+// 32 words; the planning kernels walk it one 32-word round per warp.  One
+// bitmap serves a whole run: k_bin clears the bits it takes, the relax
+// kernels set the bits of changed vertices for the next iteration.
+constexpr int kBitmapPadWords = 32;
 
 // Edge tiles of the load-balanced relax kernels.
 constexpr int kRelaxBlock = 256;
@@ -48,7 +49,8 @@ struct alignas(16) Summary {
     unsigned long long route_entry_base[kRoutes];// first index of each route in the list
     unsigned long long route_tile_base[kRoutes]; // first tile of each route
     unsigned int route_parts[kRoutes];
-    unsigned int overflow;                       // SSSP distance overflow seen
+    unsigned int pending_min;                    // bucketed SSSP: smallest pending dist
+    unsigned long long pending;                  // bucketed SSSP: active but not yet eligible
 };
 
 // Per-partition arrays, laid out right after the Summary in one buffer.
@@ -59,8 +61,9 @@ struct PartArrays {
     unsigned long long *lines;      // 128-byte lines spanned (all arrays read)
     unsigned long long *route_entry;// first list index of the partition inside its route
     unsigned long long *route_edge; // first edge index of the partition inside its route
-    unsigned long long *entry_delta;// list index = global entry prefix + entry_delta
-    unsigned long long *edge_delta; // route edge index = global edge prefix + edge_delta
+    unsigned long long *cursor;     // fill cursor: entries (low 24 bits) | edges << 24
+    unsigned long long *pending;    // bucketed SSSP: pending vertex count
+    unsigned long long *pending_inv;// bucketed SSSP: max of ~dist over pending vertices
     unsigned char *route;           // hytg_route
 };
 
@@ -111,15 +114,10 @@ __host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long 
 // ------------------------------------------------------------- launchers
 struct GraphDev {
     const unsigned long long *off;      // V+1 row offsets (device)
-    unsigned long long V, n_words, n_segs;
+    unsigned long long V, n_words_alloc;
     const unsigned int *part_wb;        // partition bounds in bitmap words, N+1
     const unsigned long long *part_eb;  // partition bounds in edges, N+1
     unsigned int N;
-};
-
-struct SegArrays {
-    unsigned long long *entries, *edges;           // per segment totals (pass 1)
-    unsigned long long *entry_prefix, *edge_prefix;// exclusive prefixes (select)
 };
 
 struct AlgoState {
@@ -135,16 +133,16 @@ struct AlgoState {
     // hub_rep[(smid % kHubReplicas) * n_hub_rep + v], summed into delta once per iteration
     float *hub_rep;
     unsigned int n_hub_rep;
+    unsigned int bucket_limit;  // SSSP delta-stepping: only dist < limit is eligible (~0u: off)
 };
 constexpr unsigned int kHubReplicas = 256;
 
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
-                         const SegArrays &sa, unsigned long long m, cudaStream_t s);
-cudaError_t launch_select(const GraphDev &g, const PartArrays &pa, const SegArrays &sa,
-                          const CostParams &cp, Summary *sum, cudaStream_t s);
+                         unsigned long long m, cudaStream_t s);
+cudaError_t launch_select(const GraphDev &g, const PartArrays &pa, const CostParams &cp,
+                          Summary *sum, cudaStream_t s);
 cudaError_t launch_bin(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
-                       const SegArrays &sa, const ListArrays &la, const Summary *sum,
-                       cudaStream_t s);
+                       const ListArrays &la, const Summary *sum, cudaStream_t s);
 
 // Edge source of a relax / gather launch.
 enum EdgeMode : int { kModeHost = 0, kModeDevice = 1, kModeCompact = 2 };
@@ -174,6 +172,9 @@ cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float 
 cudaError_t launch_pr_frontier(const AlgoState &st, unsigned long long V,
                                unsigned long long n_words_alloc, cudaStream_t s);
 cudaError_t launch_hub_reduce(const AlgoState &st, cudaStream_t s);
+cudaError_t launch_cc_jump(const AlgoState &st, unsigned long long n_words_alloc, cudaStream_t s);
+cudaError_t launch_cc_final(const AlgoState &st, unsigned long long V, unsigned int *tmp,
+                            unsigned int *out, cudaStream_t s);
 cudaError_t launch_to_original(const unsigned int *perm, const unsigned int *in, float *out,
                                unsigned long long V, cudaStream_t s);
 cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *bm,

@@ -99,11 +99,10 @@ struct hytg_ctx {
     uint64_t n_tiles_alloc = 0;
     double *d_prsums = nullptr;
     float *d_out = nullptr;                              // normalised PageRank
-    unsigned long long n_segs = 0, n_words_alloc = 0;
+    unsigned long long n_words_alloc = 0;
     // lists
     unsigned long long *d_ebase = nullptr, *d_soff = nullptr;
     unsigned int *d_pay = nullptr, *d_tiles = nullptr;
-    unsigned long long *d_seg = nullptr;                 // 4 arrays of n_segs
     // summary + per-partition arrays
     void *d_sumbuf = nullptr;
     void *h_sumbuf[2] = {};
@@ -125,6 +124,8 @@ struct hytg_ctx {
     double timing = 0;
     double hub_frac = 0.08;                              // Sec. VI-A: top 8 % of vertices
     double hub_replicas = 4096;                          // hub ids with per-SM accumulators
+    double sssp_delta = -1;                              // bucket width; -1 auto, 0 off
+    uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
     bool have_result = false;
@@ -168,7 +169,7 @@ void free_graph(hytg_ctx *c) {
     c->m_dst = c->m_w = nullptr;
     dfree(c->d_off); dfree(c->d_val); dfree(c->d_delta); dfree(c->d_bm[0]); dfree(c->d_bm[1]);
     dfree(c->d_out); dfree(c->d_ebase); dfree(c->d_soff); dfree(c->d_pay); dfree(c->d_tiles);
-    dfree(c->d_seg); dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm);
+    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm);
     dfree(c->d_hub_rep);
     c->n_hub_rep = 0;
     c->permuted = false;
@@ -198,9 +199,12 @@ void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &
 
 // Layout of the summary buffer: Summary, then per-partition arrays; the
 // prefix up to `route` is copied to the host each iteration.
+// Layout of the summary buffer: the Summary, then the per-partition arrays.
+// [n_act, pend_inv] is zeroed before every count; the whole buffer is copied
+// to the host once per iteration.
 struct SumLayout {
-    size_t n_act, entries, edges, lines, route_entry, route_edge, route, host_end, entry_delta,
-        edge_delta, total;
+    size_t n_act, entries, edges, lines, cursor, pending, pend_inv, zero_end, route_entry,
+        route_edge, route, host_end, total;
 };
 SumLayout sum_layout(uint32_t N) {
     SumLayout L;
@@ -210,12 +214,14 @@ SumLayout sum_layout(uint32_t N) {
     L.entries = o; o += a;
     L.edges = o; o += a;
     L.lines = o; o += a;
+    L.cursor = o; o += a;
+    L.pending = o; o += 8;
+    L.pend_inv = o; o += 8;
+    L.zero_end = o;
     L.route_entry = o; o += a;
     L.route_edge = o; o += a;
     L.route = o; o += ((size_t)N + 15) & ~size_t(15);
     L.host_end = o;
-    L.entry_delta = o; o += a;
-    L.edge_delta = o; o += a;
     L.total = o;
     return L;
 }
@@ -231,8 +237,9 @@ PartArrays part_arrays(hytg_ctx *c) {
     pa.route_entry = (unsigned long long *)(b + L.route_entry);
     pa.route_edge = (unsigned long long *)(b + L.route_edge);
     pa.route = (unsigned char *)(b + L.route);
-    pa.entry_delta = (unsigned long long *)(b + L.entry_delta);
-    pa.edge_delta = (unsigned long long *)(b + L.edge_delta);
+    pa.cursor = (unsigned long long *)(b + L.cursor);
+    pa.pending = (unsigned long long *)(b + L.pending);
+    pa.pending_inv = (unsigned long long *)(b + L.pend_inv);
     return pa;
 }
 
@@ -386,21 +393,11 @@ GraphDev graph_dev(hytg_ctx *c) {
     GraphDev g;
     g.off = c->d_off;
     g.V = c->V;
-    g.n_words = (c->V + 31) / 32;
-    g.n_segs = c->n_segs;
+    g.n_words_alloc = c->n_words_alloc;
     g.part_wb = c->d_part_wb;
     g.part_eb = c->d_part_eb;
     g.N = (unsigned int)(c->part_vb.size() - 1);
     return g;
-}
-
-SegArrays seg_arrays(hytg_ctx *c) {
-    SegArrays s;
-    s.entries = c->d_seg;
-    s.edges = c->d_seg + c->n_segs;
-    s.entry_prefix = c->d_seg + 2 * c->n_segs;
-    s.edge_prefix = c->d_seg + 3 * c->n_segs;
-    return s;
 }
 
 ListArrays list_arrays(hytg_ctx *c) {
@@ -432,7 +429,7 @@ CostParams cost_params(hytg_ctx *c, int algo, uint32_t iteration) {
     return p;
 }
 
-AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
+AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFFFFu) {
     AlgoState st;
     st.algo = algo;
     st.val = c->d_val;
@@ -440,8 +437,9 @@ AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
     st.delta = c->d_delta;
     st.damping = (float)c->pr_damping;
     st.eps = (float)c->pr_eps;
-    st.bm_cur = c->d_bm[cur];
-    st.bm_next = c->d_bm[cur ^ 1];
+    st.bm_cur = c->d_bm[0];
+    st.bm_next = c->d_bm[0];
+    st.bucket_limit = bucket_limit;
     st.overflow = c->d_overflow;
     st.n_arrays = (algo == kSSSP) ? 2 : 1;
     st.perm = c->d_perm;
@@ -454,16 +452,15 @@ AlgoState algo_state(hytg_ctx *c, int algo, int cur) {
 // Issue planning for one iteration on s_main: counts, selection, summary
 // copy (-> ev_sum[buf]), binning (-> ev_bin), and the device-sized cache and
 // zero-copy relaxes.
-hytg_status issue_plan(hytg_ctx *c, int algo, int cur, uint32_t it, int buf, bool with_work) {
+hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, int buf, bool with_work) {
     if (c->timing != 0 && with_work) {
         cudaEvent_t e = pool_event(c);
         CK(cudaEventRecord(e, c->s_main));
         c->iter_ev.push_back(e);
     }
     GraphDev g = graph_dev(c);
-    AlgoState st = algo_state(c, algo, cur);
+    AlgoState st = algo_state(c, algo, bucket);
     PartArrays pa = part_arrays(c);
-    SegArrays sa = seg_arrays(c);
     ListArrays la = list_arrays(c);
     Summary *sum = (Summary *)c->d_sumbuf;
     const uint32_t N = g.N;
@@ -472,13 +469,20 @@ hytg_status issue_plan(hytg_ctx *c, int algo, int cur, uint32_t it, int buf, boo
         CK(launch_hub_reduce(st, c->s_main));
         CK(launch_pr_frontier(st, c->V, c->n_words_alloc, c->s_main));
     }
-    CK(cudaMemsetAsync(pa.n_act, 0, (size_t)N * 8 * 4, c->s_main));
-    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_count(g, st, pa, sa, (unsigned long long)c->m, c->s_main)); }
-    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_select(g, pa, sa, cost_params(c, algo, it), sum, c->s_main)); }
+    if (algo == kCC && it > 0 && with_work) {
+        ScopedTime t(c, HYTG_K_OTHER, c->s_main);
+        CK(launch_cc_jump(st, c->n_words_alloc, c->s_main));
+    }
+    {
+        const SumLayout L = sum_layout(N);
+        CK(cudaMemsetAsync(pa.n_act, 0, L.zero_end - L.n_act, c->s_main));
+    }
+    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_count(g, st, pa, (unsigned long long)c->m, c->s_main)); }
+    { ScopedTime t(c, HYTG_K_COUNT, c->s_main); CK(launch_select(g, pa, cost_params(c, algo, it), sum, c->s_main)); }
     CK(cudaMemcpyAsync(c->h_sumbuf[buf], c->d_sumbuf, c->sum_host_bytes, cudaMemcpyDeviceToHost, c->s_main));
     CK(cudaEventRecord(c->ev_sum[buf], c->s_main));
     if (!with_work) return HYTG_OK;
-    { ScopedTime t(c, HYTG_K_BIN, c->s_main); CK(launch_bin(g, st, pa, sa, la, sum, c->s_main)); }
+    { ScopedTime t(c, HYTG_K_BIN, c->s_main); CK(launch_bin(g, st, pa, la, sum, c->s_main)); }
     CK(cudaEventRecord(c->ev_bin, c->s_main));
     const int cap = 152 * 4;
     if (c->carve.n_cached > 0) {
@@ -660,8 +664,7 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         c->weighted = weights != nullptr;
         c->part_edges = std::max<uint64_t>(1, (uint64_t)(c->part_bytes / 4));
         make_partitions(c);
-        c->n_segs = (V + kSegVerts - 1) / kSegVerts;
-        c->n_words_alloc = c->n_segs * kSegWords;
+        c->n_words_alloc = ((V + 31) / 32 + kBitmapPadWords - 1) / kBitmapPadWords * kBitmapPadWords;
         CK(cudaMalloc(&c->d_off, (V + 1) * 8));
         CK(cudaMemcpy(c->d_off, c->h_off.data(), (V + 1) * 8, cudaMemcpyHostToDevice));
         if (c->permuted) {
@@ -676,21 +679,25 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         CK(cudaMalloc(&c->d_val, V * 4));
         CK(cudaMalloc(&c->d_delta, V * 4));
         CK(cudaMalloc(&c->d_out, V * 4));
-        for (int i = 0; i < 2; ++i) {
-            CK(cudaMalloc(&c->d_bm[i], c->n_words_alloc * 4));
-            CK(cudaMemset(c->d_bm[i], 0, c->n_words_alloc * 4));
-        }
+        CK(cudaMalloc(&c->d_bm[0], c->n_words_alloc * 4));
+        CK(cudaMemset(c->d_bm[0], 0, c->n_words_alloc * 4));
         CK(cudaMalloc(&c->d_ebase, V * 8));
         CK(cudaMalloc(&c->d_soff, V * 8));
         CK(cudaMalloc(&c->d_pay, V * 4));
         const uint64_t n_tiles = E / kTile + 8;
         CK(cudaMalloc(&c->d_tiles, n_tiles * 4));
         c->n_tiles_alloc = n_tiles;
-        CK(cudaMalloc(&c->d_seg, c->n_segs * 4 * 8));
         hytg_status s = upload_partitions(c);
         if (s != HYTG_OK) return s;
-        c->vertex_bytes = (V + 1) * 8 + 3 * V * 4 + 2 * c->n_words_alloc * 4 + V * 20 + n_tiles * 4 +
-                          c->n_segs * 32 + c->sum_dev_bytes;
+        c->vertex_bytes = (V + 1) * 8 + 3 * V * 4 + c->n_words_alloc * 4 + V * 20 + n_tiles * 4 +
+                          c->sum_dev_bytes;
+        if (c->weighted) {
+            // automatic SSSP bucket width: 8 x the mean edge weight (delta-stepping)
+            long double sw = 0;
+            for (uint64_t e = 0; e < E; e += std::max<uint64_t>(1, E / 4096)) sw += weights[e];
+            const uint64_t ns = (E + std::max<uint64_t>(1, E / 4096) - 1) / std::max<uint64_t>(1, E / 4096);
+            c->auto_delta = ns ? (uint64_t)std::max<long double>(1.0L, 8.0L * sw / ns) : 1;
+        }
         c->loaded = true;
         return HYTG_OK;
     } catch (...) {
@@ -731,7 +738,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "MR") { if (v < 1 || v != std::floor(v)) return bad(); c->MR = v; }
     else if (k == "k") { if (v < 1 || v > 1024 || v != std::floor(v)) return bad(); c->k = v; c->carve = Carve(); }
     else if (k == "part_bytes") {
-        if (v < 4 || v > 1e12) return bad();
+        if (v < 4 || v >= 64.0 * 1024 * 1024) return bad();   // < 2^24 edges per partition
         c->part_bytes = v;
         if (c->loaded) {
             c->part_edges = std::max<uint64_t>(1, (uint64_t)(v / 4));
@@ -750,6 +757,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "max_iters") { if (v < 1) return bad(); c->max_iters = v; }
     else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
     else if (k == "hub_frac") { if (v < 0 || v > 1) return bad(); c->hub_frac = v; }
+    else if (k == "sssp_delta") { if (!(v == -1 || v >= 0) || v != std::floor(v) || v > 4e9) return bad(); c->sssp_delta = v; }
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
@@ -775,6 +783,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "max_iters") *v = c->max_iters;
     else if (k == "timing") *v = c->timing;
     else if (k == "hub_frac") *v = c->hub_frac;
+    else if (k == "sssp_delta") *v = c->sssp_delta;
     else if (k == "hub_replicas") *v = c->hub_replicas;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
@@ -812,12 +821,15 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         s = ensure_cache(c, n_arrays);
         if (s != HYTG_OK) return s;
         Carve &cv = c->carve;
-        int cur = 0;
+        // delta-stepping bucket (SSSP only): eligible vertices have dist < bucket
+        uint64_t delta = 0;
+        if (algo == kSSSP) delta = c->sssp_delta < 0 ? c->auto_delta : (uint64_t)c->sssp_delta;
+        unsigned int bucket = delta ? (unsigned int)std::min<uint64_t>(delta, 0xFFFFFFFEull) : 0xFFFFFFFFu;
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
         if ((algo == kPR || algo == kPPR) && c->d_hub_rep)
             CK(cudaMemsetAsync(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4, c->s_main));
         {
-            AlgoState st = algo_state(c, algo, cur);
+            AlgoState st = algo_state(c, algo);
             ScopedTime t(c, HYTG_K_INIT, c->s_main);
             CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
         }
@@ -825,7 +837,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
         const uint64_t ebytes = 4ull * n_arrays;
         uint32_t it = 0;
-        s = issue_plan(c, algo, cur, it, 0, true);
+        s = issue_plan(c, algo, bucket, it, 0, true);
         if (s != HYTG_OK) return s;
         std::vector<int> f_streams_used;
         for (;;) {
@@ -833,7 +845,18 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             CK(cudaEventSynchronize(c->ev_sum[buf]));
             const char *hb = (const char *)c->h_sumbuf[buf];
             const Summary *hs = (const Summary *)hb;
-            if (hs->n_active == 0) break;
+            if (hs->n_active == 0) {
+                if (hs->pending == 0) break;
+                // the current bucket is settled: open the next one at the
+                // smallest pending distance (delta-stepping)
+                const uint64_t nb = std::max<uint64_t>((uint64_t)bucket, hs->pending_min) + delta;
+                bucket = (unsigned int)std::min<uint64_t>(nb, 0xFFFFFFFEull);
+                if (hs->pending_min >= 0xFFFFFFFEull) bucket = 0xFFFFFFFFu;
+                ++it;
+                s = issue_plan(c, algo, bucket, it, it & 1, true);
+                if (s != HYTG_OK) return s;
+                continue;
+            }
             if (it >= (uint32_t)c->max_iters) { c->stats.status = HYTG_OK; break; }
             const unsigned long long *p_edges = (const unsigned long long *)(hb + L.edges);
             const unsigned long long *p_rentry = (const unsigned long long *)(hb + L.route_entry);
@@ -841,7 +864,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             const unsigned char *p_route = (const unsigned char *)(hb + L.route);
             hytg_iter_record rec{};
             rec.active_vertices = hs->n_active;
-            AlgoState st = algo_state(c, algo, cur);
+            AlgoState st = algo_state(c, algo, bucket);
             ListArrays la = list_arrays(c);
             Summary *dsum = (Summary *)c->d_sumbuf;
             // --- F: task combination (Alg. 1, k consecutive partitions, slot capacity)
@@ -943,18 +966,19 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             rec.link_bytes = f_bytes + zb + cbts;
             c->iters.push_back(rec);
             // --- next iteration
-            cur ^= 1;
             ++it;
-            s = issue_plan(c, algo, cur, it, it & 1, true);
+            s = issue_plan(c, algo, bucket, it, it & 1, true);
             if (s != HYTG_OK) return s;
         }
         c->stats.iterations = it;
         // finalisation
         {
-            AlgoState st = algo_state(c, algo, cur);
+            AlgoState st = algo_state(c, algo);
             ScopedTime t(c, HYTG_K_FINAL, c->s_main);
             if (algo == kPR || algo == kPPR)
                 CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
+            else if (algo == kCC)
+                CK(launch_cc_final(st, c->V, c->d_pay, (unsigned int *)c->d_out, c->s_main));
             else
                 CK(launch_to_original(st.perm, c->d_val, c->d_out, c->V, c->s_main));
         }
@@ -1032,7 +1056,7 @@ hytg_status hytg_fetch_pagerank_state(hytg_ctx *c, float *rank, float *delta, ui
         CK(cudaMemcpyAsync(delta, c->d_out, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
     }
     {
-        AlgoState st = algo_state(c, c->last_algo, 0);
+        AlgoState st = algo_state(c, c->last_algo);
         CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
     }
     CK(cudaStreamSynchronize(c->s_main));
@@ -1101,7 +1125,7 @@ hytg_status hytg_plan(hytg_ctx *c, hytg_algo algo_in, const uint8_t *active, uin
     if (e == cudaSuccess) e = launch_upload_bitmap(d_act, c->d_bm[0], c->V, c->n_words_alloc, c->s_main);
     if (e != cudaSuccess) { cudaFree(d_act); return fail(c, HYTG_ERR_CUDA, cudaGetErrorString(e)); }
     c->have_result = false;
-    s = issue_plan(c, algo, 0, 0, 0, false);
+    s = issue_plan(c, algo, 0xFFFFFFFFu, 0, 0, false);
     cudaStreamSynchronize(c->s_main);
     cudaFree(d_act);
     if (s != HYTG_OK) return s;

@@ -17,7 +17,7 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
         switch (st.algo) {
             case kBFS:
             case kSSSP: st.val[v] = (v == source) ? 0u : 0xFFFFFFFFu; break;
-            case kCC: st.val[v] = st.perm ? st.perm[v] : (unsigned int)v; break;  // original id
+            case kCC: st.val[v] = (unsigned int)v; break;   // internal id, mapped at the end
             case kPR: st.rank[v] = 0.0f; st.delta[v] = base; break;
             default: st.rank[v] = 0.0f; st.delta[v] = (v == source) ? base : 0.0f; break;
         }
@@ -33,7 +33,6 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
             bits = 1u << (source & 31);
         }
         st.bm_cur[w] = bits;
-        st.bm_next[w] = 0u;
     }
     if (t0 == 0) *st.overflow = 0u;
 }
@@ -51,6 +50,49 @@ __global__ void k_pr_frontier(AlgoState st, unsigned long long V, unsigned long 
         const unsigned int bits = __ballot_sync(0xffffffffu, act);
         if (lane == 0) st.bm_cur[base >> 5] = bits;
     }
+}
+
+// CC pointer jumping over the vertices changed in the last iteration: a
+// label is always the id of a vertex of the same component that is not
+// larger than the vertex itself, so label[label[v]] is a valid, no larger
+// label for v.  Jumping collapses label chains that min-label propagation
+// alone would walk one edge per iteration on high-diameter graphs; the
+// vertices it changes are already in the frontier and push their new label.
+__global__ void k_cc_jump(AlgoState st, unsigned long long n_words_alloc) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         w < n_words_alloc; w += stride) {
+        unsigned int bits = st.bm_cur[w];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const unsigned long long v = w * 32 + b;
+            const unsigned int l0 = __ldcg(&st.val[v]);
+            unsigned int l = l0;
+            for (int hop = 0; hop < 64; ++hop) {
+                const unsigned int l2 = __ldcg(&st.val[l]);
+                if (l2 >= l) break;
+                l = l2;
+            }
+            if (l < l0) atomicMin(&st.val[v], l);
+        }
+    }
+}
+
+// CC labels (smallest internal id of each component) to the smallest
+// original id of the component, in original vertex order.
+__global__ void k_cc_min_orig(AlgoState st, unsigned long long V, unsigned int *tmp) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += stride)
+        atomicMin(&tmp[st.val[v]], st.perm ? st.perm[v] : (unsigned int)v);
+}
+__global__ void k_cc_write(AlgoState st, unsigned long long V, const unsigned int *tmp,
+                           unsigned int *out) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += stride)
+        out[st.perm ? st.perm[v] : v] = tmp[st.val[v]];
 }
 
 // Fold the per-SM hub replicas into delta and clear them.
@@ -169,6 +211,20 @@ cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float 
 cudaError_t launch_hub_reduce(const AlgoState &st, cudaStream_t s) {
     if (!st.hub_rep || st.n_hub_rep == 0) return cudaSuccess;
     k_hub_reduce<<<(st.n_hub_rep + 255) / 256, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cc_jump(const AlgoState &st, unsigned long long n_words_alloc, cudaStream_t s) {
+    k_cc_jump<<<grid_for(n_words_alloc, 256), 256, 0, s>>>(st, n_words_alloc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cc_final(const AlgoState &st, unsigned long long V, unsigned int *tmp,
+                            unsigned int *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(tmp, 0xFF, V * 4, s);
+    if (e != cudaSuccess) return e;
+    k_cc_min_orig<<<grid_for(V, 256), 256, 0, s>>>(st, V, tmp);
+    k_cc_write<<<grid_for(V, 256), 256, 0, s>>>(st, V, tmp, out);
     return cudaGetLastError();
 }
 

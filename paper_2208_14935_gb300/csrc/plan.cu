@@ -1,14 +1,20 @@
 // Cost-aware task generation on the device (Sec. V-A, Alg. 1, cost part):
-//   k_count   frontier bitmap -> per-partition |A_i|, active edges, 128-byte
-//             lines (footnote to Eq. 3), and per-segment totals for the
-//             ordered compaction;
+//   k_count   frontier bitmap -> per-partition |A_i|, active edges and
+//             128-byte lines (footnote to Eq. 3);
 //   k_select  one block: the engine of every partition from Eq. 1-3 and the
-//             selection rule, then the prefix sums that place each partition's
-//             active vertices in its route's list ("pre-combine on GPU",
-//             Alg. 1 lines for Vc and Vz);
+//             selection rule, then the prefix sums that give each partition
+//             its place in its route's list ("pre-combine on GPU", Alg. 1
+//             lines for Vc and Vz);
 //   k_bin     writes the route lists (edge base, row offset, pushed value)
 //             and the tile index of the load-balanced relax kernels, takes the
-//             delta of delta-PageRank, and clears the consumed bitmap.
+//             delta of delta-PageRank, and clears the bits it consumed.
+// A partition's slice of its route list is filled through one 64-bit cursor
+// per partition (entries in the low 24 bits, edges above), so a warp
+// reserves the entry range and the edge range of a word in one atomic.
+//
+// Bucketed SSSP (delta-stepping): with a bucket limit B, only active
+// vertices with dist < B are eligible; the others stay set in the bitmap and
+// are counted as pending, with their smallest distance, for the next bucket.
 #include "common.cuh"
 #include "cost_model.cuh"
 
@@ -29,49 +35,67 @@ __device__ __forceinline__ unsigned int find_part(const unsigned int *wb, unsign
     return lo;
 }
 
+// Up to kBatch nonzero words of this warp's 32-word round, in order.
+__device__ __forceinline__ void next_batch(unsigned int &nz, unsigned int bits,
+                                           unsigned long long wbase, unsigned int (&wq)[kBatch],
+                                           unsigned long long (&wi)[kBatch]) {
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q) {
+        wq[q] = 0;
+        wi[q] = 0;
+        if (nz) {                      // warp-uniform
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            wq[q] = __shfl_sync(0xffffffffu, bits, src);
+            wi[q] = wbase + src;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArrays pa,
-                                               SegArrays sa, unsigned long long m) {
+                                               unsigned long long m) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    const unsigned int elem = 4;
-    for (unsigned long long seg = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-         seg < g.n_segs; seg += nwarps) {
-        unsigned long long seg_ent = 0, seg_edges = 0;
+    const unsigned long long n_rounds = g.n_words_alloc / 32;
+    const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
+    unsigned long long pend = 0;
+    unsigned int pend_min = 0xFFFFFFFFu;
+    for (unsigned long long rd = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+         rd < n_rounds; rd += nwarps) {
         unsigned int cur_p = 0xFFFFFFFFu;
         unsigned long long p_lo = 1, p_hi = 0;   // word range of cur_p
         unsigned long long a_nact = 0, a_ent = 0, a_edges = 0, a_lines = 0;
-        for (int r = 0; r < kSegWords / 32; ++r) {
-            const unsigned long long wbase = seg * kSegWords + r * 32;
-            const unsigned int bits = st.bm_cur[wbase + lane];
-            unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
-            while (nz) {
-                unsigned int wq[kBatch];
-                unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
+        const unsigned long long wbase = rd * 32;
+        const unsigned int bits = st.bm_cur[wbase + lane];
+        unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
+        while (nz) {
+            unsigned int wq[kBatch];
+            unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
+            unsigned int dv[kBatch];
+            next_batch(nz, bits, wbase, wq, wi);
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    wq[q] = 0;
-                    wi[q] = 0;
-                    if (nz) {                      // warp-uniform
-                        const int src = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        wq[q] = __shfl_sync(0xffffffffu, bits, src);
-                        wi[q] = wbase + src;
-                    }
+            for (int q = 0; q < kBatch; ++q) {
+                o0[q] = o1[q] = 0;
+                dv[q] = 0;
+                if ((wq[q] >> lane) & 1u) {
+                    const unsigned long long v = wi[q] * 32 + lane;
+                    o0[q] = g.off[v];
+                    o1[q] = g.off[v + 1];
+                    if (bucketed) dv[q] = st.val[v];
                 }
+            }
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    o0[q] = o1[q] = 0;
-                    if ((wq[q] >> lane) & 1u) {
-                        const unsigned long long v = wi[q] * 32 + lane;
-                        o0[q] = g.off[v];
-                        o1[q] = g.off[v + 1];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
+            for (int q = 0; q < kBatch; ++q) {
                 if (wq[q] == 0) continue;          // warp-uniform
-                const unsigned int w = wq[q];
                 const unsigned long long widx = wi[q];
+                bool act = (wq[q] >> lane) & 1u;
+                if (bucketed && act && dv[q] >= st.bucket_limit) {
+                    ++pend;
+                    pend_min = min(pend_min, dv[q]);
+                    act = false;
+                }
+                const unsigned int elig = __ballot_sync(0xffffffffu, act);
+                if (elig == 0) continue;
                 if (widx < p_lo || widx >= p_hi) {
                     if (cur_p != 0xFFFFFFFFu && lane == 0 && a_nact) {
                         atomicAdd(&pa.n_act[cur_p], a_nact);
@@ -84,30 +108,29 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
                 }
-                const unsigned long long deg = o1[q] - o0[q];
+                const unsigned long long deg = act ? o1[q] - o0[q] : 0ull;
                 const unsigned long long ln =
-                    (unsigned long long)st.n_arrays * lines_spanned(o0[q] * elem, deg * elem, m);
-                const unsigned int ent = __popc(__ballot_sync(0xffffffffu, deg > 0));
-                const unsigned long long e_sum = warp_sum_u64(deg);
-                const unsigned long long l_sum = warp_sum_u64(ln);
-                a_nact += __popc(w);
-                a_ent += ent;
-                a_edges += e_sum;
-                a_lines += l_sum;
-                seg_ent += ent;
-                seg_edges += e_sum;
-                }
+                    (unsigned long long)st.n_arrays * lines_spanned(o0[q] * 4ull, deg * 4ull, m);
+                a_nact += __popc(elig);
+                a_ent += __popc(__ballot_sync(0xffffffffu, deg > 0));
+                a_edges += warp_sum_u64(deg);
+                a_lines += warp_sum_u64(ln);
             }
         }
-        if (lane == 0) {
-            if (cur_p != 0xFFFFFFFFu && a_nact) {
-                atomicAdd(&pa.n_act[cur_p], a_nact);
-                atomicAdd(&pa.entries[cur_p], a_ent);
-                atomicAdd(&pa.edges[cur_p], a_edges);
-                atomicAdd(&pa.lines[cur_p], a_lines);
-            }
-            sa.entries[seg] = seg_ent;
-            sa.edges[seg] = seg_edges;
+        if (lane == 0 && cur_p != 0xFFFFFFFFu && a_nact) {
+            atomicAdd(&pa.n_act[cur_p], a_nact);
+            atomicAdd(&pa.entries[cur_p], a_ent);
+            atomicAdd(&pa.edges[cur_p], a_edges);
+            atomicAdd(&pa.lines[cur_p], a_lines);
+        }
+    }
+    if (bucketed) {
+        pend = warp_sum_u64(pend);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pend_min = min(pend_min, __shfl_xor_sync(0xffffffffu, pend_min, o));
+        if (lane == 0 && pend) {
+            atomicAdd(pa.pending, pend);
+            atomicMax(pa.pending_inv, (unsigned long long)(~pend_min));   // max of ~d = ~min d
         }
     }
 }
@@ -116,7 +139,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
 // Exclusive block scan of K u64 values per thread (kSelectBlock threads).
 template <int K>
 __device__ void block_scan_excl(unsigned long long (&v)[K], unsigned long long (&total)[K],
-                                unsigned long long *smem /* 32 * K */) {
+                                unsigned long long *smem /* 33 * K */) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     unsigned long long incl[K];
@@ -145,9 +168,9 @@ __device__ void block_scan_excl(unsigned long long (&v)[K], unsigned long long (
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays pa, SegArrays sa,
-                                                         CostParams cp, Summary *sum) {
-    __shared__ unsigned long long smem[33 * 12];
+__global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays pa, CostParams cp,
+                                                         Summary *sum) {
+    __shared__ unsigned long long smem[33 * 11];
     const unsigned int N = g.N;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (unsigned int p = tid; p < N; p += nt)
@@ -155,30 +178,25 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
                                                          pa.edges[p], pa.lines[p], cp);
     __syncthreads();
 
-    // per-route and global prefixes over partitions (contiguous chunk per thread)
+    // per-route prefixes over partitions (contiguous chunk per thread)
     const unsigned int ppt = (N + nt - 1) / nt;
     const unsigned int p0 = min(N, tid * ppt), p1 = min(N, p0 + ppt);
-    unsigned long long v[12];
+    unsigned long long v[10];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) v[q] = 0;
-    unsigned long long lines_r[kRoutes] = {0, 0, 0, 0, 0}, parts_r[kRoutes] = {0, 0, 0, 0, 0},
-                       nact = 0;
+    for (int q = 0; q < 10; ++q) v[q] = 0;
+    unsigned long long red[11];
+#pragma unroll
+    for (int q = 0; q < 11; ++q) red[q] = 0;
     for (unsigned int p = p0; p < p1; ++p) {
         const int r = pa.route[p];
         v[r] += pa.entries[p];
         v[kRoutes + r] += pa.edges[p];
-        v[10] += pa.entries[p];
-        v[11] += pa.edges[p];
-        lines_r[r] += pa.lines[p];
-        parts_r[r] += 1;
-        nact += pa.n_act[p];
+        red[r] += pa.lines[p];
+        red[kRoutes + r] += 1;
+        red[10] += pa.n_act[p];
     }
-    unsigned long long tot[12];
-    block_scan_excl<12>(v, tot, smem);
-    unsigned long long red[11];
-#pragma unroll
-    for (int r = 0; r < kRoutes; ++r) { red[r] = lines_r[r]; red[kRoutes + r] = parts_r[r]; }
-    red[10] = nact;
+    unsigned long long tot[10];
+    block_scan_excl<10>(v, tot, smem);
     unsigned long long redtot[11];
     block_scan_excl<11>(red, redtot, smem);
 
@@ -196,28 +214,9 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
         const int r = pa.route[p];
         pa.route_entry[p] = v[r];
         pa.route_edge[p] = v[kRoutes + r];
-        pa.entry_delta[p] = ebase[r] + v[r] - v[10];      // modulo 2^64
-        pa.edge_delta[p] = v[kRoutes + r] - v[11];
         v[r] += pa.entries[p];
         v[kRoutes + r] += pa.edges[p];
-        v[10] += pa.entries[p];
-        v[11] += pa.edges[p];
     }
-
-    // exclusive prefix over bitmap segments
-    const unsigned long long S = g.n_segs;
-    const unsigned long long spt = (S + nt - 1) / nt;
-    const unsigned long long s0 = min(S, (unsigned long long)tid * spt), s1 = min(S, s0 + spt);
-    unsigned long long sv[2] = {0, 0}, stot[2];
-    for (unsigned long long s = s0; s < s1; ++s) { sv[0] += sa.entries[s]; sv[1] += sa.edges[s]; }
-    block_scan_excl<2>(sv, stot, smem);
-    for (unsigned long long s = s0; s < s1; ++s) {
-        sa.entry_prefix[s] = sv[0];
-        sa.edge_prefix[s] = sv[1];
-        sv[0] += sa.entries[s];
-        sv[1] += sa.edges[s];
-    }
-
     if (tid == 0) {
         sum->n_active = redtot[10];
         for (int r = 0; r < kRoutes; ++r) {
@@ -228,78 +227,70 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
             sum->route_entry_base[r] = ebase[r];
             sum->route_tile_base[r] = tbase[r];
         }
+        sum->pending = *pa.pending;
+        sum->pending_min = ~(unsigned int)(*pa.pending_inv);
     }
 }
 
 // ---------------------------------------------------------------- k_bin
-__global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArrays pa, SegArrays sa,
-                                             ListArrays la, const Summary *sum) {
+__global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArrays pa, ListArrays la,
+                                             const Summary *sum) {
     const int lane = threadIdx.x & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long n_rounds = g.n_words_alloc / 32;
     const bool is_pr = st.algo == kPR || st.algo == kPPR;
-    for (unsigned long long seg = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-         seg < g.n_segs; seg += nwarps) {
-        unsigned long long run_ent = sa.entry_prefix[seg], run_edg = sa.edge_prefix[seg];
+    const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
+    for (unsigned long long rd = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+         rd < n_rounds; rd += nwarps) {
         unsigned int cur_p = 0xFFFFFFFFu;
-        unsigned long long p_lo = 1, p_hi = 0, ed = 0, gd = 0, rbase = 0, tbase = 0;
-        int rp = 0;
-        for (int r = 0; r < kSegWords / 32; ++r) {
-            const unsigned long long wbase = seg * kSegWords + r * 32;
-            const unsigned int bits = st.bm_cur[wbase + lane];
-            if (bits) st.bm_cur[wbase + lane] = 0u;
-            unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
-            while (nz) {
-                // up to kBatch nonzero words at once: their loads are issued
-                // together before the per-word scans (latency hiding)
-                unsigned int wq[kBatch];
-                unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
-                unsigned int vv[kBatch];
-                float rk[kBatch];
+        unsigned long long p_lo = 1, p_hi = 0, rbase = 0, tbase = 0, pe0 = 0, pg0 = 0;
+        const unsigned long long wbase = rd * 32;
+        const unsigned int bits = st.bm_cur[wbase + lane];
+        unsigned int keep = bits;                       // bits left for a later bucket
+        unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
+        while (nz) {
+            unsigned int wq[kBatch];
+            unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
+            unsigned int vv[kBatch];
+            float rk[kBatch];
+            next_batch(nz, bits, wbase, wq, wi);
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    wq[q] = 0;
-                    wi[q] = 0;
-                    if (nz) {                      // warp-uniform
-                        const int src = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        wq[q] = __shfl_sync(0xffffffffu, bits, src);
-                        wi[q] = wbase + src;
-                    }
+            for (int q = 0; q < kBatch; ++q) {
+                o0[q] = o1[q] = 0;
+                vv[q] = 0;
+                rk[q] = 0.0f;
+                if ((wq[q] >> lane) & 1u) {
+                    const unsigned long long v = wi[q] * 32 + lane;
+                    o0[q] = g.off[v];
+                    o1[q] = g.off[v + 1];
+                    if (is_pr) { vv[q] = __float_as_uint(st.delta[v]); rk[q] = st.rank[v]; }
+                    else vv[q] = st.val[v];
                 }
+            }
 #pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    o0[q] = o1[q] = 0;
-                    vv[q] = 0;
-                    rk[q] = 0.0f;
-                    if ((wq[q] >> lane) & 1u) {
-                        const unsigned long long v = wi[q] * 32 + lane;
-                        o0[q] = g.off[v];
-                        o1[q] = g.off[v + 1];
-                        if (is_pr) { vv[q] = __float_as_uint(st.delta[v]); rk[q] = st.rank[v]; }
-                        else vv[q] = st.val[v];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
+            for (int q = 0; q < kBatch; ++q) {
                 if (wq[q] == 0) continue;          // warp-uniform
-                const unsigned int w = wq[q];
                 const unsigned long long widx = wi[q];
+                bool act = (wq[q] >> lane) & 1u;
+                if (bucketed && act && vv[q] >= st.bucket_limit) act = false;
+                const unsigned int elig = __ballot_sync(0xffffffffu, act);
+                if (elig == 0) continue;
+                if (lane == (int)(widx - wbase)) keep = wq[q] & ~elig;
                 if (widx < p_lo || widx >= p_hi) {
                     cur_p = find_part(g.part_wb, g.N, widx);
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
-                    rp = pa.route[cur_p];
-                    ed = pa.entry_delta[cur_p];
-                    gd = pa.edge_delta[cur_p];
+                    const int rp = pa.route[cur_p];
                     rbase = sum->route_entry_base[rp];
                     tbase = sum->route_tile_base[rp];
+                    pe0 = pa.route_entry[cur_p];
+                    pg0 = pa.route_edge[cur_p];
                 }
-                const bool active = (w >> lane) & 1u;
                 const unsigned long long v = widx * 32 + lane;
-                const unsigned long long deg = o1[q] - o0[q];
+                const unsigned long long deg = act ? o1[q] - o0[q] : 0ull;
                 unsigned int pay = 0;
-                if (active) {
+                if (act) {
                     if (is_pr) {
                         // take the accumulated delta (Sec. VI-A delta-based PageRank)
                         const float dl = __uint_as_float(vv[q]);
@@ -310,12 +301,16 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                         pay = vv[q];
                     }
                 }
-                const bool is_ent = deg > 0;
-                const unsigned int bal = __ballot_sync(0xffffffffu, is_ent);
+                const unsigned int bal = __ballot_sync(0xffffffffu, deg > 0);
                 const unsigned long long incl = warp_scan_u64(deg);
-                if (is_ent) {
-                    const unsigned long long idx = run_ent + __popc(bal & lt_mask) + ed;
-                    const unsigned long long eb = run_edg + (incl - deg) + gd;
+                const unsigned long long w_edges = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long old = 0;
+                if (lane == 0 && bal)
+                    old = atomicAdd(&pa.cursor[cur_p], (w_edges << 24) | (unsigned long long)__popc(bal));
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (deg > 0) {
+                    const unsigned long long idx = rbase + pe0 + (old & 0xFFFFFFull) + __popc(bal & lt_mask);
+                    const unsigned long long eb = pg0 + (old >> 24) + (incl - deg);
                     const unsigned long long t0 = (eb + kTile - 1) / kTile;
                     const unsigned long long t1 = (eb + deg - 1) / kTile;
                     if (idx >= la.cap_entries || (t0 <= t1 && tbase + t1 >= la.cap_tiles)) {
@@ -328,39 +323,37 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                         for (unsigned long long t = t0; t <= t1; ++t) la.tile_first[tbase + t] = rel;
                     }
                 }
-                run_ent += __popc(bal);
-                run_edg += __shfl_sync(0xffffffffu, incl, 31);
-                }
             }
         }
+        if (keep != bits) st.bm_cur[wbase + lane] = keep;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
-                         const SegArrays &sa, unsigned long long m, cudaStream_t s) {
-    if (g.n_segs == 0) return cudaSuccess;
-    const unsigned long long warps = g.n_segs;
-    unsigned long long blocks = (warps + 7) / 8;
+                         unsigned long long m, cudaStream_t s) {
+    const unsigned long long rounds = g.n_words_alloc / 32;
+    if (rounds == 0) return cudaSuccess;
+    unsigned long long blocks = (rounds + 7) / 8;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
-    k_count<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, sa, m);
+    k_count<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_select(const GraphDev &g, const PartArrays &pa, const SegArrays &sa,
-                          const CostParams &cp, Summary *sum, cudaStream_t s) {
-    k_select<<<1, kSelectBlock, 0, s>>>(g, pa, sa, cp, sum);
+cudaError_t launch_select(const GraphDev &g, const PartArrays &pa, const CostParams &cp,
+                          Summary *sum, cudaStream_t s) {
+    k_select<<<1, kSelectBlock, 0, s>>>(g, pa, cp, sum);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
-                       const SegArrays &sa, const ListArrays &la, const Summary *sum,
-                       cudaStream_t s) {
-    if (g.n_segs == 0) return cudaSuccess;
-    unsigned long long blocks = (g.n_segs + 7) / 8;
+                       const ListArrays &la, const Summary *sum, cudaStream_t s) {
+    const unsigned long long rounds = g.n_words_alloc / 32;
+    if (rounds == 0) return cudaSuccess;
+    unsigned long long blocks = (rounds + 7) / 8;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
-    k_bin<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, sa, la, sum);
+    k_bin<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, la, sum);
     return cudaGetLastError();
 }
 

@@ -223,6 +223,39 @@ def test_without_hub_sorting(hy, rmat16, rmat16_sym, algo):
     e.close()
 
 
+@pytest.mark.parametrize("delta", [0, 1, 7, 100, -1])
+def test_sssp_delta_stepping(hy, rmat16, delta):
+    """Bucketed SSSP (any bucket width, 0 = one bucket) reaches the same distances."""
+    e = engine(hy, rmat16, edge_bytes(rmat16, "sssp") // 4, sssp_delta=delta)
+    for src in (0, 17):
+        check(rmat16, "sssp", e.run("sssp", src), src)
+    e.close()
+
+
+@pytest.mark.parametrize("delta", [0, 50, 1000, -1])
+def test_mesh_sssp_buckets(hy, delta):
+    g = gg.mesh(300, 200, shortcut_frac=0.001, radius=16, wmax=1000)
+    e = engine(hy, g, g.E * 8 // 5, part_bytes=16384, sssp_delta=delta)
+    check(g, "sssp", e.run("sssp", 0))
+    e.close()
+
+
+def test_cc_long_chain(hy):
+    """A directed-both-ways path numbered in reverse: min-label propagation alone
+    needs one iteration per vertex; pointer jumping must give the same labels."""
+    n = 5000
+    src = np.concatenate([np.arange(1, n), np.arange(0, n - 1)])
+    dst = np.concatenate([np.arange(0, n - 1), np.arange(1, n)])
+    order = np.lexsort((dst, src))
+    off = np.concatenate([[0], np.cumsum(np.bincount(src, minlength=n))]).astype(np.uint64)
+    g = gg.CSR(n, len(src), off, dst[order].astype(np.uint32), None)
+    for hub in (0.0, 0.08):
+        e = engine(hy, g, 1 << 20, part_bytes=4096, hub_frac=hub)
+        check(g, "cc", e.run("cc"))
+        assert e.stats()["iterations"] < n // 4
+        e.close()
+
+
 def test_budget_and_argument_errors(hy, rmat16):
     e = hy.Engine(params={"part_bytes": 64 * 1024})
     e.load(rmat16)
