@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--algos", default=",".join(ALGOS),
                     help="comma-separated subset of bfs,sssp,cc,pagerank (profiling runs)")
     ap.add_argument("--no-probe", action="store_true", help="skip the host-link probe")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain runs")
     return ap.parse_args()
 
 
@@ -160,6 +161,39 @@ def make_graphs(scale):
     return g, s
 
 
+def batched_vs_plain(hytg, eng, g, n_plain_sssp=16, n_plain_ppr=4):
+    """Batched runs (64 BFS sources, 64 SSSP sources, 32 PPR seeds, seeded
+    draws among vertices with out-edges) against the same sources run one at a
+    time, on the same engine, graph and budget.  Rate = per-source edges
+    relaxed / device time (CUDA events), i.e. the throughput a user of many
+    single-source queries gets."""
+    rng = np.random.default_rng(7)
+    cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
+    out = {}
+    for algo, k, n_plain in (("bfs", 64, 64), ("sssp", 64, n_plain_sssp), ("ppr", 32, n_plain_ppr)):
+        src = rng.choice(cand, k, replace=False).tolist()
+        a = hytg.ALGOS[algo]
+        hytg.hytg_run(eng.ctx, a, src)                       # warm-up
+        b_ms, b_edges = 0.0, 0
+        for _ in range(2):
+            hytg.hytg_run(eng.ctx, a, src)
+            st = eng.stats()
+            b_ms += st["device_ms"]
+            b_edges += st["source_edges"]
+        p_ms, p_edges = 0.0, 0
+        for v in src[:n_plain]:
+            hytg.hytg_run(eng.ctx, a, [v])
+            st = eng.stats()
+            p_ms += st["device_ms"]
+            p_edges += st["edges_relaxed"]
+        bg = b_edges / (b_ms * 1e-3) / 1e9
+        pg = p_edges / (p_ms * 1e-3) / 1e9
+        out[algo] = {"sources": k, "batched_gteps": bg, "batched_ms": b_ms / 2,
+                     "plain_gteps": pg, "plain_ms_per_source": p_ms / n_plain,
+                     "plain_sources_timed": n_plain, "speedup": bg / pg if pg else None}
+    return out
+
+
 # ------------------------------------------------------- reference arm ----
 def cpu_oracle_sample(g, budget_s: float = 20.0):
     """The oracle (plain single-threaded C) on a bounded sample: BFS from 0,
@@ -260,6 +294,7 @@ def main():
         steps.append(one_step(True))
     barrier(world)
     clk = clocks.stop()
+    batched = None if args.no_batched else batched_vs_plain(hytg, eng, g)
     # the link probe runs after the timed region (it pins and frees 1 GiB)
     memcpy_gbs, zc_gbs = (float("nan"), float("nan")) if args.no_probe else eng.probe_link(1 << 30, 10)
 
@@ -351,7 +386,7 @@ def main():
         "host_link": {"achieved_gbs": link_gbs, "memcpy_probe_gbs": memcpy_gbs,
                       "zerocopy_probe_gbs": zc_gbs, "frac_of_measured": link_gbs / memcpy_gbs,
                       "bytes_per_step": link_per_step},
-        "batched_vs_plain": None,
+        "batched_vs_plain": batched,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d + link_per_step,

@@ -89,6 +89,10 @@ typedef struct hytg_stats {
     double pr_rank_sum;               /* PageRank/PPR: sum of raw ranks */
     double device_ms;                 /* CUDA-event time of the run on its main stream, which
                                          joins every other stream of the run */
+    uint64_t source_edges;            /* batched runs: sum over sources of the edges relaxed
+                                         for that source; else edges_relaxed */
+    uint32_t n_sources;               /* sources of the run (1 unless batched) */
+    uint32_t pad_;
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -156,16 +160,21 @@ hytg_status hytg_get_param(hytg_ctx *ctx, const char *key, double *value);
 
 /* Run `algo` to convergence (Sec. IV: cost-aware task generation and task
  * scheduling alternate until no vertex is active).  sources: n_sources
- * vertex ids (host memory); BFS/SSSP/PPR take exactly one, CC/PAGERANK
- * ignore them (pass NULL, 0).  The result stays on the device until
- * hytg_fetch_result.  Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no
+ * vertex ids (host memory); BFS and SSSP take 1..64 sources, PPR 1..32
+ * seeds, CC/PAGERANK ignore them (pass NULL, 0).  With more than one source
+ * the run is batched: the planner works on the union of the sources'
+ * frontiers, so every partition transfer serves all sources at once (BFS:
+ * 64-bit source masks per vertex; SSSP and PPR: one warp per edge with a lane
+ * per source); delta-stepping is not used in batched SSSP.  The result stays
+ * on the device until hytg_fetch_result.  Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no
  * budget), HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_CUDA. */
 hytg_status hytg_run(hytg_ctx *ctx, hytg_algo algo, const uint32_t *sources, uint32_t n_sources);
 
 /* Copy the last run's result into caller-owned host memory `out` of
- * out_bytes >= 4*V bytes: uint32 per vertex (BFS level, SSSP distance, CC
- * label; HYTG_UNREACHED when unreached) or float per vertex (PageRank/PPR,
- * normalised to sum 1).  HYTG_ERR_STATE if no run completed. */
+ * out_bytes >= 4*V*n_sources bytes, source-major (out[s * V + v]): uint32 per
+ * vertex (BFS level, SSSP distance, CC label; HYTG_UNREACHED when unreached)
+ * or float per vertex (PageRank/PPR, normalised to sum 1 per source).
+ * HYTG_ERR_STATE if no run completed. */
 hytg_status hytg_fetch_result(hytg_ctx *ctx, void *out, uint64_t out_bytes);
 
 /* Raw delta-PageRank state of the last PageRank/PPR run: rank and the

@@ -1,0 +1,332 @@
+// Batched runs: up to 64 BFS or SSSP sources, or up to 32 personalised
+// PageRank seeds, share one run and therefore every partition transfer.  The
+// planner works on the union frontier (bit v set when v is active for any
+// source), so each partition's edges cross the host link once per iteration
+// for all sources together.
+//
+// Per-vertex state, vertex-major so that one vertex's sources are contiguous:
+//   BFS/SSSP  fr[v], vis[v], nxt[v]  64-bit source masks (frontier, reached,
+//             reached or improved this iteration); val[v * 64 + s] level or
+//             distance of source s.
+//   PPR       delta[v * 32 + s], rank[v * 32 + s], msg[v * 32 + s] (the push
+//             of seed s taken this iteration), fr32[v] mask of seeds taken.
+#include "common.cuh"
+#include "relax_tile.cuh"
+
+namespace hytg {
+
+namespace {
+
+inline unsigned int grid_for(unsigned long long n, unsigned int block) {
+    unsigned long long g = (n + block - 1) / block;
+    if (g > 152ull * 32) g = 152ull * 32;
+    return g == 0 ? 1u : (unsigned int)g;
+}
+
+__global__ void k_b_init(BatchState b, unsigned long long V, unsigned long long n_words_alloc,
+                         unsigned int *bm) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (b.mode == kBatchPPR) {
+        for (unsigned long long i = t0; i < V * 32; i += stride) {
+            b.delta[i] = 0.0f;
+            b.rank[i] = 0.0f;
+        }
+        for (unsigned long long v = t0; v < V; v += stride) b.fr32[v] = 0;
+    } else {
+        for (unsigned long long i = t0; i < V * 64; i += stride) b.val[i] = 0xFFFFFFFFu;
+        for (unsigned long long v = t0; v < V; v += stride) {
+            b.fr[v] = 0;
+            b.vis[v] = 0;
+            b.nxt[v] = 0;
+        }
+    }
+    for (unsigned long long w = t0; w < n_words_alloc; w += stride) bm[w] = 0;
+}
+
+// Sources (internal ids) enter the frontier.  One thread per source.
+__global__ void k_b_sources(BatchState b, const unsigned int *src, unsigned int K, float base,
+                            unsigned int *bm) {
+    const unsigned int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= K) return;
+    const unsigned int v = src[s];
+    if (b.mode == kBatchPPR) {
+        b.delta[(unsigned long long)v * 32 + s] = base;
+    } else {
+        atomicOr(&b.fr[v], 1ull << s);
+        atomicOr(&b.vis[v], 1ull << s);
+        b.val[(unsigned long long)v * 64 + s] = 0u;
+    }
+    atomicOr(&bm[v >> 5], 1u << (v & 31));
+}
+
+// BFS/SSSP after an iteration: the improved sources of v become its frontier.
+// BFS also records the level of each newly reached source.  One warp per 32
+// vertices so the bitmap word is written whole (the binning pass cleared it).
+__global__ void k_b_commit(BatchState b, unsigned long long V, unsigned long long n_words_alloc,
+                           unsigned int level, unsigned int *bm) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+         w < n_words_alloc; w += nw) {
+        const unsigned long long v = w * 32 + lane;
+        unsigned long long n = 0;
+        if (v < V) {
+            n = b.nxt[v];
+            if (b.mode == kBatchBFS && n) {
+                n &= ~b.vis[v];
+                b.vis[v] |= n;
+                unsigned long long m = n;
+                while (m) {
+                    const int s = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    b.val[v * 64 + s] = level;
+                }
+            }
+            b.fr[v] = n;
+            if (b.nxt[v]) b.nxt[v] = 0;
+        }
+        const unsigned int word = __ballot_sync(0xffffffffu, n != 0);
+        if (lane == 0) bm[w] = word;
+    }
+}
+
+// PPR: for every vertex marked in the bitmap, take the residual of each seed
+// above eps (rank += delta, delta = 0, msg = d * delta / D_o) and keep the
+// vertex in the frontier iff some seed was taken.  One warp per bitmap word,
+// lanes are seeds.
+__global__ void k_b_take(BatchState b, const unsigned long long *off, unsigned long long n_words_alloc,
+                         unsigned int K, float damping, float eps, unsigned int *bm) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+         w < n_words_alloc; w += nw) {
+        unsigned int bits = bm[w];
+        if (bits == 0) continue;
+        unsigned int keep = 0;
+        while (bits) {
+            const int bit = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const unsigned long long v = w * 32 + bit;
+            const unsigned long long deg = off[v + 1] - off[v];
+            const unsigned long long i = v * 32 + lane;
+            float dl = b.delta[i];
+            const bool act = lane < (int)K && dl > eps;
+            float msg = 0.0f;
+            if (act) {
+                b.delta[i] = 0.0f;
+                b.rank[i] += dl;
+                msg = deg ? damping * dl / (float)deg : 0.0f;
+            }
+            b.msg[i] = msg;
+            const unsigned int mask = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) b.fr32[v] = mask;
+            if (mask) keep |= 1u << bit;
+        }
+        if (lane == 0) bm[w] = keep;
+    }
+}
+
+// Multi-source BFS relax: one thread per edge; the sources of u not yet
+// reached at v are ORed into nxt[v].
+__global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListArrays la,
+                                                             const Summary *sum, RelaxTask t) {
+    __shared__ TileSmem<true> sm;
+    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
+    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    if (kb >= ke) return;
+    const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
+    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
+        unsigned long long k0;
+        const int n = tile_setup<true>(sm, la, sum, t, tile, kb, ke, &k0);
+        unsigned int dv[kRelaxIPT];
+        unsigned long long fv[kRelaxIPT];
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j) {
+            const int slot = threadIdx.x + j * kRelaxBlock;
+            dv[j] = kInf;
+            fv[j] = 0;
+            if (slot < n) {
+                const int i = sm.sid[slot];
+                const long long e = (long long)(k0 + slot) + sm.delta[i];
+                if (e >= 0 && (unsigned long long)e < t.src_len) {
+                    dv[j] = __ldg(t.dst + e);
+                    fv[j] = sm.pay[i];
+                } else {
+                    atomicOr(la.err, 8u);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRelaxIPT; ++j) {
+            if (dv[j] == kInf) continue;
+            const unsigned long long nb = fv[j] & ~__ldcg(&b.vis[dv[j]]);
+            if (nb) atomicOr(&b.nxt[dv[j]], nb);
+        }
+        __syncthreads();
+    }
+}
+
+// Multi-source SSSP and batched PPR relax: one warp per edge, lanes are
+// sources (SSSP: s = lane and lane + 32; PPR: s = lane).  A warp loads 32
+// edges at once (coalesced) and then walks them with shuffles.
+template <int MODE>
+__global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, ListArrays la,
+                                                              const Summary *sum, RelaxTask t,
+                                                              unsigned int *bm,
+                                                              unsigned int *overflow) {
+    __shared__ TileSmem<true> sm;
+    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
+    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    if (kb >= ke) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
+    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
+        unsigned long long k0;
+        const int n = tile_setup<true>(sm, la, sum, t, tile, kb, ke, &k0);
+        const int per_warp = kTile / (kRelaxBlock / 32);           // 256 slots
+        for (int c = wid * per_warp; c < (wid + 1) * per_warp && c < n; c += 32) {
+            const int slot = c + lane;
+            unsigned int dj = kInf, wj = 0, uj = 0;
+            unsigned long long fj = 0;
+            if (slot < n) {
+                const int i = sm.sid[slot];
+                const long long e = (long long)(k0 + slot) + sm.delta[i];
+                if (e >= 0 && (unsigned long long)e < t.src_len) {
+                    dj = __ldg(t.dst + e);
+                    if (MODE == kBatchSSSP) wj = __ldg(t.w + e);
+                    uj = sm.vid[i];
+                    fj = sm.pay[i];
+                } else {
+                    atomicOr(la.err, 8u);
+                }
+            }
+            const int cnt = min(32, n - c);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const unsigned int v = __shfl_sync(0xffffffffu, dj, jj);
+                if (v == kInf) continue;                               // warp-uniform
+                const unsigned int u = __shfl_sync(0xffffffffu, uj, jj);
+                const unsigned long long f = __shfl_sync(0xffffffffu, fj, jj);
+                if (MODE == kBatchSSSP) {
+                    const unsigned int w = __shfl_sync(0xffffffffu, wj, jj);
+                    unsigned long long imp = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int s = lane + 32 * h;
+                        bool better = false;
+                        if ((f >> s) & 1ull) {
+                            const unsigned long long nd =
+                                (unsigned long long)__ldcg(&b.val[(unsigned long long)u * 64 + s]) + w;
+                            if (nd >= 0xFFFFFFFEull) {
+                                *overflow = 1u;
+                            } else if ((unsigned int)nd < __ldcg(&b.val[(unsigned long long)v * 64 + s])) {
+                                atomicMin(&b.val[(unsigned long long)v * 64 + s], (unsigned int)nd);
+                                better = true;
+                            }
+                        }
+                        imp |= (unsigned long long)__ballot_sync(0xffffffffu, better) << (32 * h);
+                    }
+                    if (lane == 0 && imp) atomicOr(&b.nxt[v], imp);
+                } else {
+                    if ((f >> lane) & 1ull)
+                        atomicAdd(&b.delta[(unsigned long long)v * 32 + lane],
+                                  b.msg[(unsigned long long)u * 32 + lane]);
+                    if (lane == 0 && f) atomicOr(&bm[v >> 5], 1u << (v & 31));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_b_out(BatchState b, unsigned long long V, unsigned int K, const unsigned int *perm,
+                        unsigned int *out) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < V * K;
+         i += stride) {
+        const unsigned long long s = i / V, v = i % V;
+        const unsigned long long ov = perm ? perm[v] : v;
+        out[s * V + ov] = b.val[v * 64 + s];
+    }
+}
+
+__global__ void k_b_pr_sums(BatchState b, unsigned long long V, unsigned int K, double *sums) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    double acc = 0.0, res = 0.0;
+    for (unsigned long long v = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; v < V;
+         v += nw) {
+        acc += b.rank[v * 32 + lane];
+        res += fabs((double)b.delta[v * 32 + lane]);
+    }
+    if (lane < (int)K) {
+        atomicAdd(&sums[lane], acc);
+        atomicAdd(&sums[32 + lane], res);
+    }
+}
+
+__global__ void k_b_pr_out(BatchState b, unsigned long long V, unsigned int K, const unsigned int *perm,
+                           const double *sums, float *out) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < V * K;
+         i += stride) {
+        const unsigned long long s = i / V, v = i % V;
+        const unsigned long long ov = perm ? perm[v] : v;
+        const double S = sums[s];
+        out[s * V + ov] = S > 0.0 ? (float)((double)b.rank[v * 32 + s] / S) : 0.0f;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_b_init(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
+                          const unsigned int *src_dev, unsigned int K, float base, unsigned int *bm,
+                          cudaStream_t s) {
+    k_b_init<<<grid_for(V * (b.mode == kBatchPPR ? 32 : 64), 256), 256, 0, s>>>(b, V, n_words_alloc, bm);
+    k_b_sources<<<1, 64, 0, s>>>(b, src_dev, K, base, bm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_commit(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
+                            unsigned int level, unsigned int *bm, cudaStream_t s) {
+    k_b_commit<<<grid_for(n_words_alloc * 32, 256), 256, 0, s>>>(b, V, n_words_alloc, level, bm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_take(const BatchState &b, const unsigned long long *off,
+                          unsigned long long n_words_alloc, unsigned int K, float damping, float eps,
+                          unsigned int *bm, cudaStream_t s) {
+    k_b_take<<<grid_for(n_words_alloc * 32, 256), 256, 0, s>>>(b, off, n_words_alloc, K, damping, eps, bm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, const Summary *sum,
+                                 const RelaxTask &t, int grid_cap, unsigned int *bm,
+                                 unsigned int *overflow, cudaStream_t s) {
+    unsigned int grid = (unsigned int)grid_cap;
+    if (!t.device_sized) {
+        if (t.k_begin >= t.k_end) return cudaSuccess;
+        const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
+        if (tiles < grid) grid = (unsigned int)tiles;
+    }
+    if (b.mode == kBatchBFS) k_relax_msbfs<<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t);
+    else if (b.mode == kBatchSSSP)
+        k_relax_mswarp<kBatchSSSP><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
+    else k_relax_mswarp<kBatchPPR><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_finalize(const BatchState &b, unsigned long long V, unsigned int K,
+                              const unsigned int *perm, void *out, double *sums, cudaStream_t s) {
+    if (b.mode == kBatchPPR) {
+        cudaError_t e = cudaMemsetAsync(sums, 0, 64 * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        k_b_pr_sums<<<grid_for(V * 32, 256), 256, 0, s>>>(b, V, K, sums);
+        k_b_pr_out<<<grid_for(V * K, 256), 256, 0, s>>>(b, V, K, perm, sums, (float *)out);
+    } else {
+        k_b_out<<<grid_for(V * K, 256), 256, 0, s>>>(b, V, K, perm, (unsigned int *)out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hytg

@@ -77,6 +77,8 @@ struct ListArrays {
     unsigned long long cap_entries; // capacity of ebase / soff / pay
     unsigned long long cap_tiles;   // capacity of tile_first
     unsigned int *err;              // device word: nonzero if an index check failed
+    unsigned long long *pay64;      // batched runs: per-source frontier word of the entry
+    unsigned int *vid;              // batched runs: the entry's vertex
 };
 
 // ------------------------------------------------------------------ helpers
@@ -134,6 +136,21 @@ struct AlgoState {
     float *hub_rep;
     unsigned int n_hub_rep;
     unsigned int bucket_limit;  // SSSP delta-stepping: only dist < limit is eligible (~0u: off)
+    // batched runs (BatchMode): k_bin takes the per-source frontier word as payload
+    int batch_mode;
+    const unsigned long long *b_fr;   // BFS/SSSP: 64-bit source mask per vertex
+    const unsigned int *b_fr32;       // PPR: 32-bit seed mask per vertex
+    unsigned long long *src_work;     // sum over entries of popcount(mask) * degree
+};
+
+enum BatchMode : int { kBatchNone = 0, kBatchBFS = 1, kBatchSSSP = 2, kBatchPPR = 3 };
+
+struct BatchState {
+    int mode;
+    unsigned long long *fr, *vis, *nxt;   // BFS/SSSP source masks
+    unsigned int *val;                    // BFS level / SSSP distance, [v * 64 + s]
+    float *delta, *rank, *msg;            // PPR, [v * 32 + s]
+    unsigned int *fr32;                   // PPR seeds taken at v this iteration
 };
 constexpr unsigned int kHubReplicas = 256;
 
@@ -164,6 +181,20 @@ cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summar
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
                           cudaStream_t s);
+
+cudaError_t launch_b_init(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
+                          const unsigned int *src_dev, unsigned int K, float base, unsigned int *bm,
+                          cudaStream_t s);
+cudaError_t launch_b_commit(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
+                            unsigned int level, unsigned int *bm, cudaStream_t s);
+cudaError_t launch_b_take(const BatchState &b, const unsigned long long *off,
+                          unsigned long long n_words_alloc, unsigned int K, float damping, float eps,
+                          unsigned int *bm, cudaStream_t s);
+cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, const Summary *sum,
+                                 const RelaxTask &t, int grid_cap, unsigned int *bm,
+                                 unsigned int *overflow, cudaStream_t s);
+cudaError_t launch_b_finalize(const BatchState &b, unsigned long long V, unsigned int K,
+                              const unsigned int *perm, void *out, double *sums, cudaStream_t s);
 
 cudaError_t launch_init(const AlgoState &st, unsigned long long V, unsigned long long n_words_alloc,
                         unsigned int source, cudaStream_t s);

@@ -82,6 +82,18 @@ struct hytg_ctx {
     float *d_hub_rep = nullptr;                          // kHubReplicas x n_hub_rep floats
     unsigned int n_hub_rep = 0;
 
+    // batched runs (several sources in one run, sharing every transfer)
+    BatchState bs{};
+    bool bs_alloc_mask = false, bs_alloc_ppr = false;
+    int batch_mode = kBatchNone;
+    unsigned int batch_K = 0;
+    unsigned int *d_src = nullptr;                       // 64 source ids
+    unsigned long long *d_pay64 = nullptr;
+    unsigned int *d_vid = nullptr;
+    void *d_bout = nullptr;                              // K x V results
+    unsigned long long *d_src_work = nullptr;
+    double *d_bsums = nullptr;
+
     // partitions
     uint64_t part_edges = 0, max_part_edges = 0;
     std::vector<uint64_t> part_vb, part_eb;
@@ -172,6 +184,12 @@ void free_graph(hytg_ctx *c) {
     dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm);
     dfree(c->d_hub_rep);
     c->n_hub_rep = 0;
+    dfree(c->bs.fr); dfree(c->bs.vis); dfree(c->bs.nxt); dfree(c->bs.val);
+    dfree(c->bs.delta); dfree(c->bs.rank); dfree(c->bs.msg); dfree(c->bs.fr32);
+    dfree(c->d_pay64); dfree(c->d_vid); dfree(c->d_bout);
+    c->bs = BatchState{};
+    c->bs_alloc_mask = c->bs_alloc_ppr = false;
+    c->batch_mode = kBatchNone;
     c->permuted = false;
     c->n_hubs = 0;
     c->h_perm.clear();
@@ -409,6 +427,8 @@ ListArrays list_arrays(hytg_ctx *c) {
     l.cap_entries = c->V;
     l.cap_tiles = c->n_tiles_alloc;
     l.err = c->d_err;
+    l.pay64 = c->d_pay64;
+    l.vid = c->d_vid;
     return l;
 }
 
@@ -440,6 +460,10 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     st.bm_cur = c->d_bm[0];
     st.bm_next = c->d_bm[0];
     st.bucket_limit = bucket_limit;
+    st.batch_mode = c->batch_mode;
+    st.b_fr = c->bs.fr;
+    st.b_fr32 = c->bs.fr32;
+    st.src_work = c->d_src_work;
     st.overflow = c->d_overflow;
     st.n_arrays = (algo == kSSSP) ? 2 : 1;
     st.perm = c->d_perm;
@@ -447,6 +471,40 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     st.hub_rep = pr ? c->d_hub_rep : nullptr;
     st.n_hub_rep = pr && c->d_hub_rep ? c->n_hub_rep : 0;
     return st;
+}
+
+cudaError_t relax_any(hytg_ctx *c, const AlgoState &st, const ListArrays &la, const Summary *sum,
+                      const RelaxTask &t, int cap, cudaStream_t s) {
+    if (c->batch_mode != kBatchNone)
+        return launch_relax_batched(c->bs, la, sum, t, cap, st.bm_cur, st.overflow, s);
+    return launch_relax(st, la, sum, t, cap, s);
+}
+
+// Device arrays of batched runs, allocated on first use and kept with the graph.
+hytg_status ensure_batch(hytg_ctx *c, int mode) {
+    const uint64_t V = c->V;
+    if (!c->d_pay64) {
+        CK(cudaMalloc(&c->d_pay64, V * 8));
+        CK(cudaMalloc(&c->d_vid, V * 4));
+        CK(cudaMalloc(&c->d_bout, V * 64 * 4));
+    }
+    if (mode == kBatchPPR) {
+        if (!c->bs_alloc_ppr) {
+            CK(cudaMalloc(&c->bs.delta, V * 32 * 4));
+            CK(cudaMalloc(&c->bs.rank, V * 32 * 4));
+            CK(cudaMalloc(&c->bs.msg, V * 32 * 4));
+            CK(cudaMalloc(&c->bs.fr32, V * 4));
+            c->bs_alloc_ppr = true;
+        }
+    } else if (!c->bs_alloc_mask) {
+        CK(cudaMalloc(&c->bs.fr, V * 8));
+        CK(cudaMalloc(&c->bs.vis, V * 8));
+        CK(cudaMalloc(&c->bs.nxt, V * 8));
+        CK(cudaMalloc(&c->bs.val, V * 64 * 4));
+        c->bs_alloc_mask = true;
+    }
+    c->bs.mode = mode;
+    return HYTG_OK;
 }
 
 // Issue planning for one iteration on s_main: counts, selection, summary
@@ -464,7 +522,7 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
     ListArrays la = list_arrays(c);
     Summary *sum = (Summary *)c->d_sumbuf;
     const uint32_t N = g.N;
-    if ((algo == kPR || algo == kPPR) && it > 0) {
+    if ((algo == kPR || algo == kPPR) && it > 0 && c->batch_mode == kBatchNone) {
         ScopedTime t(c, HYTG_K_OTHER, c->s_main);
         CK(launch_hub_reduce(st, c->s_main));
         CK(launch_pr_frontier(st, c->V, c->n_words_alloc, c->s_main));
@@ -472,6 +530,14 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
     if (algo == kCC && it > 0 && with_work) {
         ScopedTime t(c, HYTG_K_OTHER, c->s_main);
         CK(launch_cc_jump(st, c->n_words_alloc, c->s_main));
+    }
+    if (c->batch_mode == kBatchPPR && with_work) {
+        ScopedTime t(c, HYTG_K_OTHER, c->s_main);
+        CK(launch_b_take(c->bs, c->d_off, c->n_words_alloc, c->batch_K, (float)c->pr_damping,
+                         (float)c->pr_eps, st.bm_cur, c->s_main));
+    } else if (c->batch_mode != kBatchNone && it > 0 && with_work) {
+        ScopedTime t(c, HYTG_K_OTHER, c->s_main);
+        CK(launch_b_commit(c->bs, c->V, c->n_words_alloc, it, st.bm_cur, c->s_main));
     }
     {
         const SumLayout L = sum_layout(N);
@@ -490,14 +556,14 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
         t.route = kRouteCache; t.mode = kModeDevice; t.dst = c->carve.cache_dst; t.w = c->carve.cache_w;
         t.shift = 0; t.device_sized = true; t.src_len = c->carve.cache_edges;
         ScopedTime tm(c, HYTG_K_RELAX_CACHE, c->s_main);
-        CK(launch_relax(st, la, sum, t, cap, c->s_main));
+        CK(relax_any(c, st, la, sum, t, cap, c->s_main));
     }
     {
         RelaxTask t{};
         t.route = kRouteZ; t.mode = kModeHost; t.dst = c->m_dst; t.w = c->m_w; t.shift = 0;
         t.device_sized = true; t.src_len = c->E;
         ScopedTime tm(c, HYTG_K_RELAX_Z, c->s_main);
-        CK(launch_relax(st, la, sum, t, cap, c->s_main));
+        CK(relax_any(c, st, la, sum, t, cap, c->s_main));
     }
     return HYTG_OK;
 }
@@ -554,6 +620,9 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_err, sizeof(unsigned int)));
     ck(cudaMemset(c->d_err, 0, sizeof(unsigned int)));
     ck(cudaMalloc(&c->d_prsums, 2 * sizeof(double)));
+    ck(cudaMalloc(&c->d_src, 64 * sizeof(unsigned int)));
+    ck(cudaMalloc(&c->d_src_work, sizeof(unsigned long long)));
+    ck(cudaMalloc(&c->d_bsums, 64 * sizeof(double)));
     if (s != HYTG_OK) { hytg_destroy(c); return s; }
     *out = c;
     return HYTG_OK;
@@ -568,6 +637,9 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_overflow);
     dfree(c->d_err);
     dfree(c->d_prsums);
+    dfree(c->d_src);
+    dfree(c->d_src_work);
+    dfree(c->d_bsums);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < kMaxStreams; ++i) {
         if (c->s_f[i]) cudaStreamDestroy(c->s_f[i]);
@@ -797,12 +869,20 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
     if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
     const bool needs_src = (algo == kBFS || algo == kSSSP || algo == kPPR);
     uint32_t source = 0;
+    uint32_t src_int[64] = {0};
+    int bmode = kBatchNone;
     if (needs_src) {
-        if (!sources || n_sources != 1)
-            return fail(c, HYTG_ERR_ARG, "this algorithm takes exactly one source");
-        source = sources[0];
-        if (source >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
-        if (c->permuted) source = c->h_inv[source];
+        const uint32_t max_src = algo == kPPR ? 32u : 64u;
+        if (!sources || n_sources < 1 || n_sources > max_src)
+            return fail(c, HYTG_ERR_ARG, "BFS/SSSP take 1..64 sources, PPR 1..32 seeds");
+        for (uint32_t i = 0; i < n_sources; ++i) {
+            if (sources[i] >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
+            src_int[i] = c->permuted ? c->h_inv[sources[i]] : sources[i];
+        }
+        source = src_int[0];
+        if (n_sources > 1) bmode = algo == kBFS ? kBatchBFS : algo == kSSSP ? kBatchSSSP : kBatchPPR;
+    } else {
+        n_sources = 1;
     }
     if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
     try {
@@ -814,6 +894,14 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->timed.clear();
         c->iter_ev.clear();
         c->ev_used = 0;
+        c->batch_mode = kBatchNone;
+        c->batch_K = 1;
+        if (bmode != kBatchNone) {
+            hytg_status bsx = ensure_batch(c, bmode);
+            if (bsx != HYTG_OK) return bsx;
+            c->batch_mode = bmode;
+            c->batch_K = n_sources;
+        }
         const int n_arrays = (algo == kSSSP) ? 2 : 1;
         CK(cudaEventRecord(c->ev_run[0], c->s_main));
         hytg_status s = plan_carve(c, n_arrays);
@@ -823,15 +911,24 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         Carve &cv = c->carve;
         // delta-stepping bucket (SSSP only): eligible vertices have dist < bucket
         uint64_t delta = 0;
-        if (algo == kSSSP) delta = c->sssp_delta < 0 ? c->auto_delta : (uint64_t)c->sssp_delta;
+        if (algo == kSSSP && c->batch_mode == kBatchNone)
+            delta = c->sssp_delta < 0 ? c->auto_delta : (uint64_t)c->sssp_delta;
         unsigned int bucket = delta ? (unsigned int)std::min<uint64_t>(delta, 0xFFFFFFFEull) : 0xFFFFFFFFu;
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
-        if ((algo == kPR || algo == kPPR) && c->d_hub_rep)
+        if ((algo == kPR || algo == kPPR) && c->d_hub_rep && c->batch_mode == kBatchNone)
             CK(cudaMemsetAsync(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4, c->s_main));
         {
             AlgoState st = algo_state(c, algo);
             ScopedTime t(c, HYTG_K_INIT, c->s_main);
-            CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
+            if (c->batch_mode != kBatchNone) {
+                CK(cudaMemcpyAsync(c->d_src, src_int, sizeof(src_int), cudaMemcpyHostToDevice, c->s_main));
+                CK(cudaMemsetAsync(c->d_src_work, 0, 8, c->s_main));
+                CK(cudaMemsetAsync(c->d_overflow, 0, 4, c->s_main));
+                CK(launch_b_init(c->bs, c->V, c->n_words_alloc, c->d_src, c->batch_K,
+                                 (float)(1.0 - c->pr_damping), st.bm_cur, c->s_main));
+            } else {
+                CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
+            }
         }
         const SumLayout L = sum_layout((uint32_t)(c->part_vb.size() - 1));
         const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
@@ -906,7 +1003,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 t.src_len = edges;
                 {
                     ScopedTime tm(c, HYTG_K_RELAX_F, fs);
-                    CK(launch_relax(st, la, dsum, t, 152 * 8, fs));
+                    CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
                 }
                 f_bytes += edges * ebytes;
                 ++n_tasks;
@@ -933,7 +1030,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                     r.src_len = ce - cb;
                     {
                         ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
-                        CK(launch_relax(st, la, dsum, r, 152 * 8, c->s_c));
+                        CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
                     }
                 }
                 CK(cudaEventRecord(c->ev_c, c->s_c));
@@ -975,7 +1072,9 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         {
             AlgoState st = algo_state(c, algo);
             ScopedTime t(c, HYTG_K_FINAL, c->s_main);
-            if (algo == kPR || algo == kPPR)
+            if (c->batch_mode != kBatchNone)
+                CK(launch_b_finalize(c->bs, c->V, c->batch_K, c->d_perm, c->d_bout, c->d_bsums, c->s_main));
+            else if (algo == kPR || algo == kPPR)
                 CK(launch_pr_finalize(st, c->V, c->d_out, c->d_prsums, c->s_main));
             else if (algo == kCC)
                 CK(launch_cc_final(st, c->V, c->d_pay, (unsigned int *)c->d_out, c->s_main));
@@ -986,8 +1085,11 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         double prs[2] = {0, 0};
         CK(cudaMemcpyAsync(&ovf, c->d_overflow, 4, cudaMemcpyDeviceToHost, c->s_main));
         CK(cudaMemcpyAsync(&ierr, c->d_err, 4, cudaMemcpyDeviceToHost, c->s_main));
-        if (algo == kPR || algo == kPPR)
+        if ((algo == kPR || algo == kPPR) && c->batch_mode == kBatchNone)
             CK(cudaMemcpyAsync(prs, c->d_prsums, 16, cudaMemcpyDeviceToHost, c->s_main));
+        unsigned long long swork = 0;
+        if (c->batch_mode != kBatchNone)
+            CK(cudaMemcpyAsync(&swork, c->d_src_work, 8, cudaMemcpyDeviceToHost, c->s_main));
         CK(cudaEventRecord(c->ev_run[1], c->s_main));
         CK(cudaStreamSynchronize(c->s_main));
         CK(cudaGetLastError());
@@ -1000,6 +1102,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats.wall_ms = std::chrono::duration<double, std::milli>(t_end - t_start).count();
         c->stats.pr_rank_sum = prs[0];
         c->stats.pr_residual_sum = prs[1];
+        c->stats.n_sources = c->batch_K;
+        c->stats.source_edges = c->batch_mode != kBatchNone ? swork : c->stats.edges_relaxed;
         for (size_t i = 0; i + 1 < c->iter_ev.size() && i < c->iters.size(); ++i) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, c->iter_ev[i], c->iter_ev[i + 1]) == cudaSuccess)
@@ -1033,17 +1137,19 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
 hytg_status hytg_fetch_result(hytg_ctx *c, void *out, uint64_t out_bytes) {
     if (!c || !out) return HYTG_ERR_ARG;
     if (!c->have_result) return fail(c, HYTG_ERR_STATE, "no completed run");
-    if (out_bytes < c->V * 4) return fail(c, HYTG_ERR_ARG, "output buffer too small");
+    const uint64_t need = c->V * 4 * (c->batch_mode != kBatchNone ? c->batch_K : 1);
+    if (out_bytes < need) return fail(c, HYTG_ERR_ARG, "output buffer too small");
     CK(cudaSetDevice(c->device));
-    CK(cudaMemcpyAsync(out, c->d_out, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaMemcpyAsync(out, c->batch_mode != kBatchNone ? c->d_bout : (void *)c->d_out, need,
+                       cudaMemcpyDeviceToHost, c->s_main));
     CK(cudaStreamSynchronize(c->s_main));
     return HYTG_OK;
 }
 
 hytg_status hytg_fetch_pagerank_state(hytg_ctx *c, float *rank, float *delta, uint64_t V) {
     if (!c) return HYTG_ERR_ARG;
-    if (!c->have_result || !(c->last_algo == kPR || c->last_algo == kPPR))
-        return fail(c, HYTG_ERR_STATE, "no completed PageRank run");
+    if (!c->have_result || !(c->last_algo == kPR || c->last_algo == kPPR) || c->batch_mode != kBatchNone)
+        return fail(c, HYTG_ERR_STATE, "no completed single-source PageRank run");
     if (V < c->V) return fail(c, HYTG_ERR_ARG, "buffers too small");
     CK(cudaSetDevice(c->device));
     // original vertex order; d_out (the normalised result) is rebuilt afterwards

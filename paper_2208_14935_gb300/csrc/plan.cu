@@ -239,8 +239,10 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
     const unsigned int lt_mask = (1u << lane) - 1u;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long n_rounds = g.n_words_alloc / 32;
-    const bool is_pr = st.algo == kPR || st.algo == kPPR;
+    const bool batched = st.batch_mode != kBatchNone;
+    const bool is_pr = !batched && (st.algo == kPR || st.algo == kPPR);
     const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
+    unsigned long long work = 0;
     for (unsigned long long rd = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
          rd < n_rounds; rd += nwarps) {
         unsigned int cur_p = 0xFFFFFFFFu;
@@ -254,17 +256,20 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
             unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
             unsigned int vv[kBatch];
             float rk[kBatch];
+            unsigned long long bf[kBatch];
             next_batch(nz, bits, wbase, wq, wi);
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
                 o0[q] = o1[q] = 0;
                 vv[q] = 0;
                 rk[q] = 0.0f;
+                bf[q] = 0;
                 if ((wq[q] >> lane) & 1u) {
                     const unsigned long long v = wi[q] * 32 + lane;
                     o0[q] = g.off[v];
                     o1[q] = g.off[v + 1];
-                    if (is_pr) { vv[q] = __float_as_uint(st.delta[v]); rk[q] = st.rank[v]; }
+                    if (batched) bf[q] = st.batch_mode == kBatchPPR ? st.b_fr32[v] : st.b_fr[v];
+                    else if (is_pr) { vv[q] = __float_as_uint(st.delta[v]); rk[q] = st.rank[v]; }
                     else vv[q] = st.val[v];
                 }
             }
@@ -319,6 +324,11 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                         la.ebase[idx] = eb;
                         la.soff[idx] = o0[q];
                         la.pay[idx] = pay;
+                        if (batched) {
+                            la.pay64[idx] = bf[q];
+                            la.vid[idx] = (unsigned int)v;
+                            work += (unsigned long long)__popcll(bf[q]) * deg;
+                        }
                         const unsigned int rel = (unsigned int)(idx - rbase);
                         for (unsigned long long t = t0; t <= t1; ++t) la.tile_first[tbase + t] = rel;
                     }
@@ -326,6 +336,10 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
             }
         }
         if (keep != bits) st.bm_cur[wbase + lane] = keep;
+    }
+    if (batched) {
+        work = warp_sum_u64(work);
+        if (lane == 0 && work) atomicAdd(st.src_work, work);
     }
 }
 

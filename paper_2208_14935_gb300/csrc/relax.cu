@@ -19,100 +19,11 @@
 //           the partition's edges are shifted by its first edge index);
 //   compact the compacted buffer, where route edge k sits at k - shift.
 #include "common.cuh"
+#include "relax_tile.cuh"
 
 namespace hytg {
 
 namespace {
-
-constexpr unsigned int kInf = 0xFFFFFFFFu;
-
-struct TileSmem {
-    long long delta[kTile + 1];          // edge address = k + delta
-    unsigned int pay[kTile + 1];
-    unsigned short sid[kTile];           // owner entry (tile-relative) of each slot
-    unsigned int wmax[kRelaxBlock / 32];
-};
-
-// Set up one tile; returns the number of edges (0 if nothing to do).
-__device__ __forceinline__ int tile_setup(TileSmem &sm, const ListArrays &la, const Summary *sum,
-                                          const RelaxTask &t, unsigned long long tile,
-                                          unsigned long long kb, unsigned long long ke,
-                                          unsigned long long *k0_out) {
-    const int r = t.route;
-    const unsigned long long rbase = sum->route_entry_base[r];
-    const unsigned long long tbase = sum->route_tile_base[r];
-    const unsigned long long n_ent = sum->route_entries[r];
-    const unsigned long long route_edges = sum->route_edges[r];
-    const unsigned long long tstart = tile * kTile;
-    const unsigned long long k0 = tstart > kb ? tstart : kb;
-    const unsigned long long tend = tstart + kTile;
-    const unsigned long long k1 = tend < ke ? tend : ke;
-    const unsigned long long i0 = (k0 == tstart) ? la.tile_first[tbase + tile] : t.first_entry;
-    const unsigned long long last_tile = (route_edges - 1) / kTile;
-    const unsigned long long i_last = (tile < last_tile) ? la.tile_first[tbase + tile + 1] : n_ent - 1;
-    const long long n_e_ll = (long long)i_last - (long long)i0 + 1;
-    if (n_e_ll < 1 || n_e_ll > kTile + 1 || i0 >= n_ent || i_last >= n_ent || k1 <= k0) {
-        // inconsistent tile index: record it and skip the tile (block-uniform)
-        if (threadIdx.x == 0) atomicOr(la.err, 1u);
-        *k0_out = k0;
-        return 0;
-    }
-    const int n_e = (int)n_e_ll;
-    const int n_slots = (int)(k1 - k0);
-    for (int j = threadIdx.x; j < kTile; j += kRelaxBlock) sm.sid[j] = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < n_e; j += kRelaxBlock) {
-        const unsigned long long i = rbase + i0 + j;
-        const unsigned long long eb = la.ebase[i];
-        long long d;
-        if (t.mode == kModeCompact) d = -t.shift;
-        else d = (long long)la.soff[i] - (long long)eb - t.shift;
-        sm.delta[j] = d;
-        sm.pay[j] = la.pay[i];
-        if (j > 0) {
-            const long long head = (long long)eb - (long long)k0;
-            if (head > 0 && head < n_slots) sm.sid[head] = (unsigned short)j;
-            else if (head <= 0) atomicOr(la.err, 4u);
-        }
-    }
-    __syncthreads();
-    // inclusive max-scan of sid over the tile (8 consecutive slots per thread)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int base = threadIdx.x * kRelaxIPT;
-    unsigned int mx = 0;
-#pragma unroll
-    for (int q = 0; q < kRelaxIPT; ++q) {
-        unsigned int x = sm.sid[base + q];
-        mx = x > mx ? x : mx;
-        sm.sid[base + q] = (unsigned short)mx;
-    }
-    unsigned int inc = mx;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc = y > inc ? y : inc;
-    }
-    if (lane == 31) sm.wmax[wid] = inc;
-    __syncthreads();
-    unsigned int carry = 0;
-    for (int q = 0; q < wid; ++q) carry = sm.wmax[q] > carry ? sm.wmax[q] : carry;
-    unsigned int excl = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane > 0) carry = excl > carry ? excl : carry;
-    if (carry) {
-#pragma unroll
-        for (int q = 0; q < kRelaxIPT; ++q)
-            if (sm.sid[base + q] < carry) sm.sid[base + q] = (unsigned short)carry;
-    }
-    __syncthreads();
-    *k0_out = k0;
-    return n_slots;
-}
-
-__device__ __forceinline__ unsigned int sm_id() {
-    unsigned int id;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
-    return id;
-}
 
 // hub_rep: this SM's replica row of the hub accumulators (PageRank only).
 template <int ALGO>
@@ -151,7 +62,7 @@ __device__ __forceinline__ void relax_edge(const AlgoState &st, unsigned int v, 
 template <int ALGO>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays la,
                                                        const Summary *sum, RelaxTask t) {
-    __shared__ TileSmem sm;
+    __shared__ TileSmem<false> sm;
     const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
     const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
     if (kb >= ke) return;
@@ -160,7 +71,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
     float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
-        const int n = tile_setup(sm, la, sum, t, tile, kb, ke, &k0);
+        const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
         unsigned int dv[kRelaxIPT], wv[kRelaxIPT], pv[kRelaxIPT];
 #pragma unroll
         for (int j = 0; j < kRelaxIPT; ++j) {
@@ -190,13 +101,13 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
 __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Summary *sum,
                                                         RelaxTask t, unsigned int *out_dst,
                                                         unsigned int *out_w) {
-    __shared__ TileSmem sm;
+    __shared__ TileSmem<false> sm;
     const unsigned long long kb = t.k_begin, ke = t.k_end;
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
-        const int n = tile_setup(sm, la, sum, t, tile, kb, ke, &k0);
+        const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
         unsigned int dv[kRelaxIPT], wv[kRelaxIPT];
 #pragma unroll
         for (int j = 0; j < kRelaxIPT; ++j) {

@@ -37,7 +37,8 @@ class hytg_stats(ctypes.Structure):
                 ("route_vertices", u64 * 5), ("route_edges", u64 * 5), ("link_bytes", u64 * 5),
                 ("cache_fill_bytes", u64), ("f_tasks", u64), ("kernel_launches", u64),
                 ("wall_ms", dbl), ("kernel_ms", dbl * 12), ("kernel_count", u64 * 12),
-                ("pr_residual_sum", dbl), ("pr_rank_sum", dbl), ("device_ms", dbl)]
+                ("pr_residual_sum", dbl), ("pr_rank_sum", dbl), ("device_ms", dbl),
+                ("source_edges", u64), ("n_sources", u32), ("pad_", u32)]
 
 
 class hytg_info(ctypes.Structure):
@@ -160,11 +161,11 @@ def hytg_run(ctx, algo: int, sources: Optional[Sequence[int]] = None):
     _check(ctx, load().hytg_run(ctx, int(algo), _ptr(src), n))
 
 
-def hytg_fetch_result(ctx, V: int, algo: int) -> np.ndarray:
+def hytg_fetch_result(ctx, V: int, algo: int, n_sources: int = 1) -> np.ndarray:
     dt = np.float32 if algo in (HYTG_PAGERANK, HYTG_PPR) else np.uint32
-    out = np.empty(V, dtype=dt)
+    out = np.empty(V * n_sources, dtype=dt)
     _check(ctx, load().hytg_fetch_result(ctx, _ptr(out), out.nbytes))
-    return out
+    return out if n_sources == 1 else out.reshape(n_sources, V)
 
 
 def hytg_fetch_pagerank_state(ctx, V: int):
@@ -301,10 +302,19 @@ class Engine:
     def get_param(self, key: str) -> float:
         return hytg_get_param(self.ctx, key)
 
-    def run(self, algo, source: Optional[int] = None) -> np.ndarray:
+    def run(self, algo, source=None) -> np.ndarray:
+        """source: None, one vertex id, or a sequence of ids (a batched run,
+        whose result has one row per source)."""
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
-        hytg_run(self.ctx, a, None if source is None else [source])
-        return hytg_fetch_result(self.ctx, self.V, a)
+        if source is None:
+            hytg_run(self.ctx, a, None)
+            return hytg_fetch_result(self.ctx, self.V, a)
+        if np.ndim(source) == 0:
+            hytg_run(self.ctx, a, [int(source)])
+            return hytg_fetch_result(self.ctx, self.V, a)
+        srcs = [int(x) for x in source]
+        hytg_run(self.ctx, a, srcs)
+        return hytg_fetch_result(self.ctx, self.V, a, len(srcs))
 
     def stats(self) -> Dict:
         return hytg_get_stats(self.ctx)
