@@ -295,6 +295,7 @@ def main():
     barrier(world)
     clk = clocks.stop()
     batched = None if args.no_batched else batched_vs_plain(hytg, eng, g)
+    red_probe = None if args.no_probe else eng.probe_atomics(1 << 28, 5)
     # the link probe runs after the timed region (it pins and frees 1 GiB)
     memcpy_gbs, zc_gbs = (float("nan"), float("nan")) if args.no_probe else eng.probe_link(1 << 30, 10)
 
@@ -334,14 +335,42 @@ def main():
                 kms[i] += p[a]["stats"]["kernel_ms"][i]
                 kcnt[i] += p[a]["stats"]["kernel_count"][i]
     peaks, peak_src = measured_peaks()
-    roofline = None
-    if not args.no_timing:
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofline, roofline_l2 = None, None
+    if not args.no_timing and "pagerank" in algos:
+        # The dominant kernel (ncu launch-list share ~53 %, profiles/) is the
+        # PageRank relax; its F-route launches (4-partition tasks staged in HBM).
+        ms_f = sum(p["pagerank"]["stats"]["kernel_ms"][4] for p in steps)
+        n_f = sum(p["pagerank"]["stats"]["kernel_count"][4] for p in steps)
+        e_f = sum(p["pagerank"]["stats"]["route_edges"][2] for p in steps)
+        v_f = sum(p["pagerank"]["stats"]["route_vertices"][2] for p in steps)
+        if ms_f > 0 and n_f > 0:
+            # algorithmic bytes: 4 B edge + 8 B value read-modify-write per edge,
+            # 20 B list entry per active vertex
+            alg = e_f * 12 + v_f * 20
+            achieved = alg / (ms_f * 1e-3) / 1e9
+            # DRAM bytes per launch from the ncu capture of the same kernel on an
+            # F task of the same size (profiles/k_relax_pagerank_rmat22.md):
+            # 30.8 MB for 4.37 M edges, scaled by this run's edges per launch
+            traffic = 30.8e6 / 4.37e6 * (e_f / n_f)
+            roofline = {"kernel": "k_relax<PageRank> F route", "bound": "hbm", "achieved": achieved,
+                        "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                        "bytes_model": "per edge 4 + 8 (value RMW), per active vertex 20",
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                        "launches": n_f, "avg_launch_us": ms_f * 1e3 / n_f,
+                        "alg_bytes_per_launch": alg / n_f}
+            if red_probe:
+                rate = e_f / (ms_f * 1e-3) / 1e9
+                roofline_l2 = {"kernel": "k_relax<PageRank> F route", "bound": "l2_reductions",
+                               "achieved": rate, "peak": red_probe[0], "unit": "G updates/s",
+                               "frac": rate / red_probe[0],
+                               "peak_source": "hytg_probe_atomics, uniform targets, same run",
+                               "skewed_targets_gops": red_probe[1]}
+    elif not args.no_timing:
         relax = {"relax_Z": 7, "relax_cache": 3, "relax_F": 4, "relax_C": 6, "gather_C": 5}
         dom = max(relax, key=lambda k: kms[relax[k]])
         route_of = {"relax_Z": 4, "relax_cache": 1, "relax_F": 2, "relax_C": 3, "gather_C": 3}
         r = route_of[dom]
-        # algorithmic bytes per relaxed edge: the edge entry (d1 = 4, SSSP 8)
-        # plus the 4-byte value read-modify-write (8 B); per list entry 20 B
         alg_bytes = 0
         for p in steps:
             for a in algos:
@@ -350,18 +379,9 @@ def main():
                 alg_bytes += st["route_edges"][r] * (d1 + 8) + st["route_vertices"][r] * 20
         ms = kms[relax[dom]]
         achieved = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-        if dom in ("relax_Z", "gather_C"):
-            roofline = {"kernel": dom, "bound": "host_link", "achieved": achieved, "peak": memcpy_gbs,
-                        "unit": "GB/s", "frac": achieved / memcpy_gbs if memcpy_gbs else None,
-                        "traffic": None, "peak_source": "pinned cudaMemcpyAsync H2D probe, same run",
-                        "launches": kcnt[relax[dom]], "ms_total": ms}
-        else:
-            hbm = float(peaks.get("hbm_gbs", 6800.0))
-            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                        "bytes_model": "per edge d1 + 8 (value RMW), per active vertex 20 (list entry)",
-                        "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                        "launches": kcnt[relax[dom]], "ms_total": ms}
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None,
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -388,6 +408,7 @@ def main():
                       "bytes_per_step": link_per_step},
         "batched_vs_plain": batched,
         "roofline": roofline,
+        "roofline_l2": roofline_l2,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d + link_per_step,
                 "d2h_bytes_per_step": d2h},

@@ -223,6 +223,14 @@ hytg_status hytg_plan(hytg_ctx *ctx, hytg_algo algo, const uint8_t *active, uint
 hytg_status hytg_probe_link(hytg_ctx *ctx, uint64_t bytes, uint32_t reps, double *memcpy_gbs,
                             double *zerocopy_gbs);
 
+/* L2 reduction probe (the ceiling of the relax kernels, which push with
+ * fire-and-forget float/integer reductions into L2-resident vertex arrays):
+ * n random `red.global.add.f32` into 2^24 floats, with uniform targets and
+ * with R-MAT-skewed targets (each of 24 index bits set with probability 0.24),
+ * best of `reps`; results in 1e9 updates/s.  Allocates device memory. */
+hytg_status hytg_probe_atomics(hytg_ctx *ctx, uint64_t n, uint32_t reps, double *uniform_gops,
+                               double *skewed_gops);
+
 /* Per-iteration record of the last run (up to cap records). */
 typedef struct hytg_iter_record {
     uint64_t active_vertices;

@@ -211,6 +211,8 @@ cudaError_t launch_to_original(const unsigned int *perm, const unsigned int *in,
 cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *bm,
                                  unsigned long long V, unsigned long long n_words_alloc,
                                  cudaStream_t s);
+cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, int skew, bool gen,
+                             cudaStream_t s);
 cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
                             int grid, cudaStream_t s);
 

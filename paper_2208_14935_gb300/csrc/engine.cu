@@ -1307,6 +1307,44 @@ hytg_status hytg_probe_link(hytg_ctx *c, uint64_t bytes, uint32_t reps, double *
     return st;
 }
 
+hytg_status hytg_probe_atomics(hytg_ctx *c, uint64_t n, uint32_t reps, double *uniform_gops,
+                               double *skewed_gops) {
+    if (!c || n < 1024 || n > (1ull << 30) || reps == 0) return HYTG_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    unsigned int *idx = nullptr;
+    float *d = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto run = [&]() -> hytg_status {
+        CK(cudaMalloc(&idx, n * 4));
+        CK(cudaMalloc(&d, (1ull << 24) * 4));
+        CK(cudaMemset(d, 0, (1ull << 24) * 4));
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        for (int skew = 0; skew < 2; ++skew) {
+            CK(launch_red_probe(idx, d, n, skew, true, c->s_main));
+            float best = 1e30f;
+            for (uint32_t r = 0; r < reps + 1; ++r) {
+                CK(cudaEventRecord(a, c->s_main));
+                CK(launch_red_probe(idx, d, n, skew, false, c->s_main));
+                CK(cudaEventRecord(b, c->s_main));
+                CK(cudaEventSynchronize(b));
+                float ms;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (r > 0) best = std::min(best, ms);
+            }
+            double *out = skew ? skewed_gops : uniform_gops;
+            if (out) *out = n / (best * 1e-3) / 1e9;
+        }
+        return HYTG_OK;
+    };
+    hytg_status st = run();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (idx) cudaFree(idx);
+    if (d) cudaFree(d);
+    return st;
+}
+
 hytg_status hytg_get_permutation(hytg_ctx *c, uint32_t *perm, uint64_t V) {
     if (!c || !perm) return HYTG_ERR_ARG;
     if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");

@@ -184,6 +184,32 @@ __global__ void k_zc_probe(const uint4 *src, unsigned long long n16, unsigned lo
     if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);
 }
 
+// L2 reduction probe: indices into a 2^24-float array, uniform or with the
+// R-MAT in-degree skew (each of 24 bits set with probability 0.24), then
+// n fire-and-forget float additions.
+__device__ __forceinline__ unsigned long long probe_mix(unsigned long long x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
+    return x;
+}
+__global__ void k_probe_idx(unsigned int *idx, unsigned long long n, int skew) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        unsigned int v = 0;
+        if (!skew) {
+            v = (unsigned int)(probe_mix(i * 2654435761ull + 7) & 0xFFFFFFull);
+        } else {
+            for (int j = 0; j < 24; ++j)
+                if ((probe_mix(i * 64 + j + 12345) & 0xFFFFFFFFull) < 1030792151ull) v |= 1u << j;
+        }
+        idx[i] = v;
+    }
+}
+__global__ void k_probe_red(const unsigned int *__restrict__ idx, unsigned long long n, float *d) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride)
+        atomicAdd(&d[__ldg(idx + i)], 1.0f);
+}
+
 inline unsigned int grid_for(unsigned long long n, unsigned int block) {
     unsigned long long g = (n + block - 1) / block;
     if (g > 152ull * 32) g = 152ull * 32;
@@ -247,6 +273,13 @@ cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *
                                  unsigned long long V, unsigned long long n_words_alloc,
                                  cudaStream_t s) {
     k_upload_bitmap<<<grid_for(n_words_alloc, 256), 256, 0, s>>>(active_dev, bm, V, n_words_alloc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, int skew, bool gen,
+                             cudaStream_t s) {
+    if (gen) k_probe_idx<<<152 * 16, 256, 0, s>>>(idx, n, skew);
+    else k_probe_red<<<152 * 32, 256, 0, s>>>(idx, n, d);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ def load(path: Optional[str] = None):
             "hytg_get_iterations": [vp, vp, u32, P(u32)],
             "hytg_hub_order": [u64, vp, vp, dbl, vp, P(u64)],
             "hytg_get_permutation": [vp, vp, u64],
+            "hytg_probe_atomics": [vp, u64, u32, P(dbl), P(dbl)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -245,6 +246,12 @@ def hytg_probe_link(ctx, nbytes: int = 1 << 30, reps: int = 10):
     return a.value, b.value
 
 
+def hytg_probe_atomics(ctx, n: int = 1 << 28, reps: int = 5):
+    a, b = dbl(), dbl()
+    _check(ctx, load().hytg_probe_atomics(ctx, int(n), reps, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def hytg_get_iterations(ctx):
     n = u32()
     _check(ctx, load().hytg_get_iterations(ctx, None, 0, ctypes.byref(n)))
@@ -341,3 +348,6 @@ class Engine:
 
     def probe_link(self, nbytes: int = 1 << 30, reps: int = 10):
         return hytg_probe_link(self.ctx, nbytes, reps)
+
+    def probe_atomics(self, n: int = 1 << 28, reps: int = 5):
+        return hytg_probe_atomics(self.ctx, n, reps)

@@ -314,3 +314,12 @@ def test_pagerank_bound_reported(hy, rmat16):
     assert B < 1e-4
     assert abs(float(rank.astype(np.float64).sum()) - st["pr_rank_sum"]) < 1e-3 * st["pr_rank_sum"]
     e.close()
+
+
+def test_probes(hy):
+    e = hy.Engine()
+    mc, zc = e.probe_link(64 << 20, 2)
+    assert mc > 1 and zc > 1
+    uni, skew = e.probe_atomics(1 << 22, 2)
+    assert uni > 1 and skew > 0.1
+    e.close()
