@@ -244,6 +244,26 @@ typedef struct hytg_iter_record {
 } hytg_iter_record;
 hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t cap, uint32_t *n);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching over a batched run.  hytg_serve_begin opens a
+ * batched run of n_slots query slots (BFS/SSSP 1..64, PPR 1..32) with empty
+ * state; hytg_serve_admit places a query (its source or seed, original id)
+ * in a free slot at the next iteration boundary; hytg_serve_step runs one
+ * iteration for every busy slot at once (one planning pass and one set of
+ * partition transfers serve them all) and reports, as bit masks over slots,
+ * the busy slots and the busy slots whose query has converged (no frontier
+ * left); hytg_serve_fetch copies a converged slot's result (V values,
+ * original vertex order: BFS level from its source, SSSP distance, PPR rank
+ * normalised to sum 1) and frees the slot; hytg_serve_end closes the run.
+ * Queries admitted while others are running join them at the next
+ * iteration, so their work overlaps on the device; a query's result does not
+ * depend on the others.  hytg_run is refused while serving. */
+hytg_status hytg_serve_begin(hytg_ctx *ctx, hytg_algo algo, uint32_t n_slots);
+hytg_status hytg_serve_admit(hytg_ctx *ctx, uint32_t slot, uint32_t source);
+hytg_status hytg_serve_step(hytg_ctx *ctx, uint64_t *finished, uint64_t *busy);
+hytg_status hytg_serve_fetch(hytg_ctx *ctx, uint32_t slot, void *out, uint64_t out_bytes);
+hytg_status hytg_serve_end(hytg_ctx *ctx);
+
 const char *hytg_status_str(hytg_status s);
 const char *hytg_last_error(hytg_ctx *ctx);
 

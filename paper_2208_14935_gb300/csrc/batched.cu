@@ -88,6 +88,12 @@ __global__ void k_b_commit(BatchState b, unsigned long long V, unsigned long lon
         }
         const unsigned int word = __ballot_sync(0xffffffffu, n != 0);
         if (lane == 0) bm[w] = word;
+        if (b.alive && word) {
+            unsigned long long orv = n;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, o);
+            if (lane == 0) atomicOr(b.alive, orv);
+        }
     }
 }
 
@@ -104,6 +110,7 @@ __global__ void k_b_take(BatchState b, const unsigned long long *off, unsigned l
         unsigned int bits = bm[w];
         if (bits == 0) continue;
         unsigned int keep = 0;
+        unsigned int seen = 0;
         while (bits) {
             const int bit = __ffs(bits) - 1;
             bits &= bits - 1;
@@ -122,8 +129,61 @@ __global__ void k_b_take(BatchState b, const unsigned long long *off, unsigned l
             const unsigned int mask = __ballot_sync(0xffffffffu, act);
             if (lane == 0) b.fr32[v] = mask;
             if (mask) keep |= 1u << bit;
+            seen |= mask;
         }
-        if (lane == 0) bm[w] = keep;
+        if (lane == 0) {
+            bm[w] = keep;
+            if (b.alive && seen) atomicOr(b.alive, (unsigned long long)seen);
+        }
+    }
+}
+
+// Serving: clear one slot's column, then seed its source (at an iteration
+// boundary: no relax of the slot is in flight, and the slot's source enters
+// through nxt / delta so that the next commit or take activates it).
+__global__ void k_serve_clear(BatchState b, unsigned long long V, unsigned int slot) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long bit = 1ull << slot;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += stride) {
+        if (b.mode == kBatchPPR) {
+            b.delta[v * 32 + slot] = 0.0f;
+            b.rank[v * 32 + slot] = 0.0f;
+        } else {
+            b.val[v * 64 + slot] = 0xFFFFFFFFu;
+            if (b.fr[v] & bit) b.fr[v] &= ~bit;
+            if (b.vis[v] & bit) b.vis[v] &= ~bit;
+            if (b.nxt[v] & bit) b.nxt[v] &= ~bit;
+        }
+    }
+}
+__global__ void k_serve_seed(BatchState b, unsigned int slot, unsigned int src, float base,
+                             unsigned int *bm) {
+    if (b.mode == kBatchPPR) {
+        b.delta[(unsigned long long)src * 32 + slot] = base;
+        atomicOr(&bm[src >> 5], 1u << (src & 31));
+    } else {
+        if (b.mode == kBatchSSSP) b.val[(unsigned long long)src * 64 + slot] = 0u;
+        atomicOr(&b.nxt[src], 1ull << slot);
+    }
+}
+
+// One finished slot's result in original vertex order: BFS levels relative to
+// the slot's admission iteration, SSSP distances, PPR ranks normalised.
+__global__ void k_serve_extract(BatchState b, unsigned long long V, unsigned int slot,
+                                const unsigned int *perm, unsigned int offset, void *out,
+                                const double *sums) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += stride) {
+        const unsigned long long ov = perm ? perm[v] : v;
+        if (b.mode == kBatchPPR) {
+            const double S = sums[slot];
+            ((float *)out)[ov] = S > 0.0 ? (float)((double)b.rank[v * 32 + slot] / S) : 0.0f;
+        } else {
+            const unsigned int x = b.val[v * 64 + slot];
+            ((unsigned int *)out)[ov] = (x == 0xFFFFFFFFu || b.mode != kBatchBFS) ? x : x - offset;
+        }
     }
 }
 
@@ -313,6 +373,25 @@ cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, cons
     else if (b.mode == kBatchSSSP)
         k_relax_mswarp<kBatchSSSP><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
     else k_relax_mswarp<kBatchPPR><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_serve_admit(const BatchState &b, unsigned long long V, unsigned int slot,
+                               unsigned int src, float base, unsigned int *bm, cudaStream_t s) {
+    k_serve_clear<<<grid_for(V, 256), 256, 0, s>>>(b, V, slot);
+    k_serve_seed<<<1, 1, 0, s>>>(b, slot, src, base, bm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_serve_extract(const BatchState &b, unsigned long long V, unsigned int slot,
+                                 const unsigned int *perm, unsigned int offset, void *out,
+                                 double *sums, cudaStream_t s) {
+    if (b.mode == kBatchPPR) {
+        cudaError_t e = cudaMemsetAsync(sums, 0, 64 * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        k_b_pr_sums<<<grid_for(V * 32, 256), 256, 0, s>>>(b, V, 32, sums);
+    }
+    k_serve_extract<<<grid_for(V, 256), 256, 0, s>>>(b, V, slot, perm, offset, out, sums);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct alignas(16) Summary {
     unsigned int route_parts[kRoutes];
     unsigned int pending_min;                    // bucketed SSSP: smallest pending dist
     unsigned long long pending;                  // bucketed SSSP: active but not yet eligible
+    unsigned long long alive;                    // batched: sources with a frontier this iteration
 };
 
 // Per-partition arrays, laid out right after the Summary in one buffer.
@@ -65,6 +66,7 @@ struct PartArrays {
     unsigned long long *pending;    // bucketed SSSP: pending vertex count
     unsigned long long *pending_inv;// bucketed SSSP: max of ~dist over pending vertices
     unsigned char *route;           // hytg_route
+    const unsigned long long *alive;// batched: source mask of the frontier (or nullptr)
 };
 
 // The list of active vertices of one iteration, grouped by route and, inside
@@ -151,6 +153,7 @@ struct BatchState {
     unsigned int *val;                    // BFS level / SSSP distance, [v * 64 + s]
     float *delta, *rank, *msg;            // PPR, [v * 32 + s]
     unsigned int *fr32;                   // PPR seeds taken at v this iteration
+    unsigned long long *alive;            // OR of every vertex's frontier mask (serving)
 };
 constexpr unsigned int kHubReplicas = 256;
 
@@ -193,6 +196,11 @@ cudaError_t launch_b_take(const BatchState &b, const unsigned long long *off,
 cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, const Summary *sum,
                                  const RelaxTask &t, int grid_cap, unsigned int *bm,
                                  unsigned int *overflow, cudaStream_t s);
+cudaError_t launch_serve_admit(const BatchState &b, unsigned long long V, unsigned int slot,
+                               unsigned int src, float base, unsigned int *bm, cudaStream_t s);
+cudaError_t launch_serve_extract(const BatchState &b, unsigned long long V, unsigned int slot,
+                                 const unsigned int *perm, unsigned int offset, void *out,
+                                 double *sums, cudaStream_t s);
 cudaError_t launch_b_finalize(const BatchState &b, unsigned long long V, unsigned int K,
                               const unsigned int *perm, void *out, double *sums, cudaStream_t s);
 

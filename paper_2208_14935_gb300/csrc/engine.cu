@@ -93,6 +93,13 @@ struct hytg_ctx {
     void *d_bout = nullptr;                              // K x V results
     unsigned long long *d_src_work = nullptr;
     double *d_bsums = nullptr;
+    unsigned long long *d_alive = nullptr;
+    // serving (continuous batching over the batched state)
+    bool serving = false;
+    int serve_algo = -1;
+    uint32_t serve_it = 0;
+    uint64_t serve_busy = 0, serve_alive = 0;
+    uint32_t serve_admit_it[64] = {};
 
     // partitions
     uint64_t part_edges = 0, max_part_edges = 0;
@@ -258,6 +265,7 @@ PartArrays part_arrays(hytg_ctx *c) {
     pa.cursor = (unsigned long long *)(b + L.cursor);
     pa.pending = (unsigned long long *)(b + L.pending);
     pa.pending_inv = (unsigned long long *)(b + L.pend_inv);
+    pa.alive = c->batch_mode != kBatchNone ? c->d_alive : nullptr;
     return pa;
 }
 
@@ -504,6 +512,7 @@ hytg_status ensure_batch(hytg_ctx *c, int mode) {
         c->bs_alloc_mask = true;
     }
     c->bs.mode = mode;
+    c->bs.alive = c->d_alive;
     return HYTG_OK;
 }
 
@@ -531,11 +540,12 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
         ScopedTime t(c, HYTG_K_OTHER, c->s_main);
         CK(launch_cc_jump(st, c->n_words_alloc, c->s_main));
     }
+    if (c->batch_mode != kBatchNone && with_work) CK(cudaMemsetAsync(c->d_alive, 0, 8, c->s_main));
     if (c->batch_mode == kBatchPPR && with_work) {
         ScopedTime t(c, HYTG_K_OTHER, c->s_main);
         CK(launch_b_take(c->bs, c->d_off, c->n_words_alloc, c->batch_K, (float)c->pr_damping,
                          (float)c->pr_eps, st.bm_cur, c->s_main));
-    } else if (c->batch_mode != kBatchNone && it > 0 && with_work) {
+    } else if (c->batch_mode != kBatchNone && (it > 0 || c->serving) && with_work) {
         ScopedTime t(c, HYTG_K_OTHER, c->s_main);
         CK(launch_b_commit(c->bs, c->V, c->n_words_alloc, it, st.bm_cur, c->s_main));
     }
@@ -584,6 +594,127 @@ hytg_status ensure_cache(hytg_ctx *c, int n_arrays) {
     return HYTG_OK;
 }
 
+// Issue one iteration's route work after its summary reached the host:
+// F tasks (task combination of Alg. 1, copy + relax per stream), the C
+// route in chunks of the compaction buffer, and the per-iteration statistics.
+// Leaves s_main waiting on every stream used.
+hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *hb, int n_arrays) {
+    const SumLayout L = sum_layout((uint32_t)(c->part_vb.size() - 1));
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    const uint64_t ebytes = 4ull * n_arrays;
+    const Summary *hs = (const Summary *)hb;
+    Carve &cv = c->carve;
+    std::vector<int> f_streams_used;
+    const unsigned long long *p_edges = (const unsigned long long *)(hb + L.edges);
+    const unsigned long long *p_rentry = (const unsigned long long *)(hb + L.route_entry);
+    const unsigned long long *p_redge = (const unsigned long long *)(hb + L.route_edge);
+    const unsigned char *p_route = (const unsigned char *)(hb + L.route);
+    hytg_iter_record rec{};
+    rec.active_vertices = hs->n_active;
+    AlgoState st = algo_state(c, algo, bucket);
+    ListArrays la = list_arrays(c);
+    Summary *dsum = (Summary *)c->d_sumbuf;
+    // --- F: task combination (Alg. 1, k consecutive partitions, slot capacity)
+    uint64_t f_bytes = 0;
+    uint32_t n_tasks = 0;
+    f_streams_used.clear();
+    uint32_t i = 0;
+    while (i < N) {
+        if (p_route[i] != kRouteF) { ++i; continue; }
+        uint32_t j = i;
+        uint64_t edges = c->part_eb[i + 1] - c->part_eb[i];
+        while (j + 1 < N && p_route[j + 1] == kRouteF && (j + 1 - i + 1) <= (uint32_t)c->k &&
+               edges + (c->part_eb[j + 2] - c->part_eb[j + 1]) <= cv.slot_edges) {
+            ++j;
+            edges += c->part_eb[j + 1] - c->part_eb[j];
+        }
+        const uint32_t slot = n_tasks % cv.n_slots;
+        cudaStream_t fs = c->s_f[slot];
+        const uint64_t e0 = c->part_eb[i];
+        {
+            // the copy needs only the route decision (already on the host)
+            // and the slot's previous relax (same stream), not the lists
+            ScopedTime t(c, HYTG_K_COPY_F, fs);
+            CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+            if (n_arrays == 2)
+                CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+        }
+        if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
+            f_streams_used.push_back((int)slot);
+            CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
+        }
+        RelaxTask t{};
+        t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
+        t.shift = (long long)e0;
+        t.k_begin = p_redge[i];
+        t.k_end = p_redge[j] + p_edges[j];
+        t.first_entry = p_rentry[i];
+        t.device_sized = false;
+        t.src_len = edges;
+        {
+            ScopedTime tm(c, HYTG_K_RELAX_F, fs);
+            CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
+        }
+        f_bytes += edges * ebytes;
+        ++n_tasks;
+        i = j + 1;
+    }
+    // --- C: gather active lists into the compaction buffer, relax, in chunks
+    const uint64_t c_edges = hs->route_edges[kRouteC];
+    if (c_edges) {
+        CK(cudaStreamWaitEvent(c->s_c, c->ev_bin, 0));
+        for (uint64_t cb = 0; cb < c_edges; cb += cv.compact_edges) {
+            const uint64_t ce = std::min<uint64_t>(c_edges, cb + cv.compact_edges);
+            RelaxTask g{};
+            g.route = kRouteC; g.mode = kModeHost; g.dst = c->m_dst; g.w = c->m_w; g.shift = 0;
+            g.k_begin = cb; g.k_end = ce; g.first_entry = 0; g.device_sized = false;
+            g.src_len = c->E;
+            {
+                ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c);
+                CK(launch_gather(la, dsum, g, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, 152 * 8, c->s_c));
+            }
+            RelaxTask r{};
+            r.route = kRouteC; r.mode = kModeCompact; r.dst = cv.cmp_dst; r.w = cv.cmp_w;
+            r.shift = (long long)cb; r.k_begin = cb; r.k_end = ce; r.first_entry = 0;
+            r.device_sized = false;
+            r.src_len = ce - cb;
+            {
+                ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
+                CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
+            }
+        }
+        CK(cudaEventRecord(c->ev_c, c->s_c));
+        CK(cudaStreamWaitEvent(c->s_main, c->ev_c, 0));
+    }
+    for (int sl : f_streams_used) {
+        CK(cudaEventRecord(c->ev_f[sl], c->s_f[sl]));
+        CK(cudaStreamWaitEvent(c->s_main, c->ev_f[sl], 0));
+    }
+    // --- statistics of this iteration
+    uint64_t act_edges = 0;
+    for (int r = 0; r < kRoutes; ++r) {
+        act_edges += hs->route_edges[r];
+        rec.route_partitions[r] = hs->route_parts[r];
+        rec.route_edges[r] = hs->route_edges[r];
+        c->stats.route_partitions[r] += hs->route_parts[r];
+        c->stats.route_vertices[r] += hs->route_entries[r];
+        c->stats.route_edges[r] += hs->route_edges[r];
+    }
+    const uint64_t zb = hs->route_lines[kRouteZ] * (uint64_t)c->m;
+    const uint64_t cbts = hs->route_lines[kRouteC] * (uint64_t)c->m;
+    c->stats.link_bytes[kRouteF] += f_bytes;
+    c->stats.link_bytes[kRouteZ] += zb;
+    c->stats.link_bytes[kRouteC] += cbts;
+    c->stats.f_tasks += n_tasks;
+    c->stats.edges_relaxed += act_edges;
+    c->stats.vertices_processed += hs->n_active;
+    rec.active_edges = act_edges;
+    rec.f_tasks = n_tasks;
+    rec.link_bytes = f_bytes + zb + cbts;
+    c->iters.push_back(rec);
+    return HYTG_OK;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -623,6 +754,7 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_src, 64 * sizeof(unsigned int)));
     ck(cudaMalloc(&c->d_src_work, sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_bsums, 64 * sizeof(double)));
+    ck(cudaMalloc(&c->d_alive, sizeof(unsigned long long)));
     if (s != HYTG_OK) { hytg_destroy(c); return s; }
     *out = c;
     return HYTG_OK;
@@ -640,6 +772,7 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_src);
     dfree(c->d_src_work);
     dfree(c->d_bsums);
+    dfree(c->d_alive);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < kMaxStreams; ++i) {
         if (c->s_f[i]) cudaStreamDestroy(c->s_f[i]);
@@ -867,6 +1000,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
     if (algo < 0 || algo > 4) return fail(c, HYTG_ERR_ARG, "unknown algorithm");
     if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
     if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
+    if (c->serving) return fail(c, HYTG_ERR_STATE, "serving in progress (hytg_serve_end first)");
     const bool needs_src = (algo == kBFS || algo == kSSSP || algo == kPPR);
     uint32_t source = 0;
     uint32_t src_int[64] = {0};
@@ -908,7 +1042,6 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         if (s != HYTG_OK) return s;
         s = ensure_cache(c, n_arrays);
         if (s != HYTG_OK) return s;
-        Carve &cv = c->carve;
         // delta-stepping bucket (SSSP only): eligible vertices have dist < bucket
         uint64_t delta = 0;
         if (algo == kSSSP && c->batch_mode == kBatchNone)
@@ -930,13 +1063,9 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
             }
         }
-        const SumLayout L = sum_layout((uint32_t)(c->part_vb.size() - 1));
-        const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
-        const uint64_t ebytes = 4ull * n_arrays;
         uint32_t it = 0;
         s = issue_plan(c, algo, bucket, it, 0, true);
         if (s != HYTG_OK) return s;
-        std::vector<int> f_streams_used;
         for (;;) {
             const int buf = it & 1;
             CK(cudaEventSynchronize(c->ev_sum[buf]));
@@ -955,113 +1084,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 continue;
             }
             if (it >= (uint32_t)c->max_iters) { c->stats.status = HYTG_OK; break; }
-            const unsigned long long *p_edges = (const unsigned long long *)(hb + L.edges);
-            const unsigned long long *p_rentry = (const unsigned long long *)(hb + L.route_entry);
-            const unsigned long long *p_redge = (const unsigned long long *)(hb + L.route_edge);
-            const unsigned char *p_route = (const unsigned char *)(hb + L.route);
-            hytg_iter_record rec{};
-            rec.active_vertices = hs->n_active;
-            AlgoState st = algo_state(c, algo, bucket);
-            ListArrays la = list_arrays(c);
-            Summary *dsum = (Summary *)c->d_sumbuf;
-            // --- F: task combination (Alg. 1, k consecutive partitions, slot capacity)
-            uint64_t f_bytes = 0;
-            uint32_t n_tasks = 0;
-            f_streams_used.clear();
-            uint32_t i = 0;
-            while (i < N) {
-                if (p_route[i] != kRouteF) { ++i; continue; }
-                uint32_t j = i;
-                uint64_t edges = c->part_eb[i + 1] - c->part_eb[i];
-                while (j + 1 < N && p_route[j + 1] == kRouteF && (j + 1 - i + 1) <= (uint32_t)c->k &&
-                       edges + (c->part_eb[j + 2] - c->part_eb[j + 1]) <= cv.slot_edges) {
-                    ++j;
-                    edges += c->part_eb[j + 1] - c->part_eb[j];
-                }
-                const uint32_t slot = n_tasks % cv.n_slots;
-                cudaStream_t fs = c->s_f[slot];
-                const uint64_t e0 = c->part_eb[i];
-                {
-                    // the copy needs only the route decision (already on the host)
-                    // and the slot's previous relax (same stream), not the lists
-                    ScopedTime t(c, HYTG_K_COPY_F, fs);
-                    CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, fs));
-                    if (n_arrays == 2)
-                        CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, fs));
-                }
-                if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
-                    f_streams_used.push_back((int)slot);
-                    CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
-                }
-                RelaxTask t{};
-                t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
-                t.shift = (long long)e0;
-                t.k_begin = p_redge[i];
-                t.k_end = p_redge[j] + p_edges[j];
-                t.first_entry = p_rentry[i];
-                t.device_sized = false;
-                t.src_len = edges;
-                {
-                    ScopedTime tm(c, HYTG_K_RELAX_F, fs);
-                    CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
-                }
-                f_bytes += edges * ebytes;
-                ++n_tasks;
-                i = j + 1;
-            }
-            // --- C: gather active lists into the compaction buffer, relax, in chunks
-            const uint64_t c_edges = hs->route_edges[kRouteC];
-            if (c_edges) {
-                CK(cudaStreamWaitEvent(c->s_c, c->ev_bin, 0));
-                for (uint64_t cb = 0; cb < c_edges; cb += cv.compact_edges) {
-                    const uint64_t ce = std::min<uint64_t>(c_edges, cb + cv.compact_edges);
-                    RelaxTask g{};
-                    g.route = kRouteC; g.mode = kModeHost; g.dst = c->m_dst; g.w = c->m_w; g.shift = 0;
-                    g.k_begin = cb; g.k_end = ce; g.first_entry = 0; g.device_sized = false;
-                    g.src_len = c->E;
-                    {
-                        ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c);
-                        CK(launch_gather(la, dsum, g, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, 152 * 8, c->s_c));
-                    }
-                    RelaxTask r{};
-                    r.route = kRouteC; r.mode = kModeCompact; r.dst = cv.cmp_dst; r.w = cv.cmp_w;
-                    r.shift = (long long)cb; r.k_begin = cb; r.k_end = ce; r.first_entry = 0;
-                    r.device_sized = false;
-                    r.src_len = ce - cb;
-                    {
-                        ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
-                        CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
-                    }
-                }
-                CK(cudaEventRecord(c->ev_c, c->s_c));
-                CK(cudaStreamWaitEvent(c->s_main, c->ev_c, 0));
-            }
-            for (int sl : f_streams_used) {
-                CK(cudaEventRecord(c->ev_f[sl], c->s_f[sl]));
-                CK(cudaStreamWaitEvent(c->s_main, c->ev_f[sl], 0));
-            }
-            // --- statistics of this iteration
-            uint64_t act_edges = 0;
-            for (int r = 0; r < kRoutes; ++r) {
-                act_edges += hs->route_edges[r];
-                rec.route_partitions[r] = hs->route_parts[r];
-                rec.route_edges[r] = hs->route_edges[r];
-                c->stats.route_partitions[r] += hs->route_parts[r];
-                c->stats.route_vertices[r] += hs->route_entries[r];
-                c->stats.route_edges[r] += hs->route_edges[r];
-            }
-            const uint64_t zb = hs->route_lines[kRouteZ] * (uint64_t)c->m;
-            const uint64_t cbts = hs->route_lines[kRouteC] * (uint64_t)c->m;
-            c->stats.link_bytes[kRouteF] += f_bytes;
-            c->stats.link_bytes[kRouteZ] += zb;
-            c->stats.link_bytes[kRouteC] += cbts;
-            c->stats.f_tasks += n_tasks;
-            c->stats.edges_relaxed += act_edges;
-            c->stats.vertices_processed += hs->n_active;
-            rec.active_edges = act_edges;
-            rec.f_tasks = n_tasks;
-            rec.link_bytes = f_bytes + zb + cbts;
-            c->iters.push_back(rec);
+            s = issue_work(c, algo, bucket, hb, n_arrays);
+            if (s != HYTG_OK) return s;
             // --- next iteration
             ++it;
             s = issue_plan(c, algo, bucket, it, it & 1, true);
@@ -1132,6 +1156,116 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
     } catch (...) {
         return fail(c, HYTG_ERR_HOSTMEM, "host allocation failed during the run");
     }
+}
+
+hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
+    if (!c) return HYTG_ERR_ARG;
+    const int algo = (int)algo_in;
+    if (algo != kBFS && algo != kSSSP && algo != kPPR)
+        return fail(c, HYTG_ERR_ARG, "serving supports BFS, SSSP and PPR");
+    if (n_slots < 1 || n_slots > (algo == kPPR ? 32u : 64u))
+        return fail(c, HYTG_ERR_ARG, "BFS/SSSP serve 1..64 slots, PPR 1..32");
+    if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
+    if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
+    if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
+    CK(cudaSetDevice(c->device));
+    const int mode = algo == kBFS ? kBatchBFS : algo == kSSSP ? kBatchSSSP : kBatchPPR;
+    hytg_status s = ensure_batch(c, mode);
+    if (s != HYTG_OK) return s;
+    c->batch_mode = mode;
+    c->batch_K = n_slots;
+    c->have_result = false;
+    c->stats = hytg_stats{};
+    c->iters.clear();
+    c->timed.clear();
+    c->iter_ev.clear();
+    c->ev_used = 0;
+    const int n_arrays = algo == kSSSP ? 2 : 1;
+    s = plan_carve(c, n_arrays);
+    if (s != HYTG_OK) return s;
+    s = ensure_cache(c, n_arrays);
+    if (s != HYTG_OK) return s;
+    CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
+    CK(cudaMemsetAsync(c->d_overflow, 0, 4, c->s_main));
+    CK(cudaMemsetAsync(c->d_src_work, 0, 8, c->s_main));
+    CK(launch_b_init(c->bs, c->V, c->n_words_alloc, c->d_src, 0, 0.0f, c->d_bm[0], c->s_main));
+    c->serving = true;
+    c->serve_algo = algo;
+    c->serve_it = 0;
+    c->serve_busy = 0;
+    c->serve_alive = 0;
+    return HYTG_OK;
+}
+
+hytg_status hytg_serve_admit(hytg_ctx *c, uint32_t slot, uint32_t source) {
+    if (!c) return HYTG_ERR_ARG;
+    if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    if (slot >= c->batch_K) return fail(c, HYTG_ERR_ARG, "slot out of range");
+    if (c->serve_busy & (1ull << slot)) return fail(c, HYTG_ERR_STATE, "slot is busy");
+    if (source >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
+    const uint32_t src = c->permuted ? c->h_inv[source] : source;
+    CK(launch_serve_admit(c->bs, c->V, slot, src, (float)(1.0 - c->pr_damping), c->d_bm[0], c->s_main));
+    c->serve_busy |= 1ull << slot;
+    c->serve_admit_it[slot] = c->serve_it;
+    return HYTG_OK;
+}
+
+hytg_status hytg_serve_step(hytg_ctx *c, uint64_t *finished, uint64_t *busy) {
+    if (!c) return HYTG_ERR_ARG;
+    if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    try {
+        const int algo = c->serve_algo;
+        const int n_arrays = algo == kSSSP ? 2 : 1;
+        const uint32_t it = c->serve_it;
+        hytg_status s = issue_plan(c, algo, 0xFFFFFFFFu, it, it & 1, true);
+        if (s != HYTG_OK) return s;
+        CK(cudaEventSynchronize(c->ev_sum[it & 1]));
+        const char *hb = (const char *)c->h_sumbuf[it & 1];
+        const Summary *hs = (const Summary *)hb;
+        c->serve_alive = hs->alive;
+        if (hs->n_active > 0) {
+            s = issue_work(c, algo, 0xFFFFFFFFu, hb, n_arrays);
+            if (s != HYTG_OK) return s;
+        }
+        c->serve_it = it + 1;
+        c->stats.iterations = c->serve_it;
+        if (finished) *finished = c->serve_busy & ~c->serve_alive;
+        if (busy) *busy = c->serve_busy;
+        return HYTG_OK;
+    } catch (...) {
+        return fail(c, HYTG_ERR_HOSTMEM, "host allocation failed");
+    }
+}
+
+hytg_status hytg_serve_fetch(hytg_ctx *c, uint32_t slot, void *out, uint64_t out_bytes) {
+    if (!c || !out) return HYTG_ERR_ARG;
+    if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    if (slot >= c->batch_K) return fail(c, HYTG_ERR_ARG, "slot out of range");
+    const uint64_t bit = 1ull << slot;
+    if (!(c->serve_busy & bit) || (c->serve_alive & bit))
+        return fail(c, HYTG_ERR_STATE, "slot has no finished query");
+    if (out_bytes < c->V * 4) return fail(c, HYTG_ERR_ARG, "output buffer too small");
+    CK(launch_serve_extract(c->bs, c->V, slot, c->d_perm, c->serve_admit_it[slot], c->d_bout,
+                            c->d_bsums, c->s_main));
+    CK(cudaMemcpyAsync(out, c->d_bout, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
+    unsigned int ovf = 0, ierr = 0;
+    CK(cudaMemcpyAsync(&ovf, c->d_overflow, 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaMemcpyAsync(&ierr, c->d_err, 4, cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaStreamSynchronize(c->s_main));
+    c->serve_busy &= ~bit;
+    if (ierr) return fail(c, HYTG_ERR_CUDA, "internal index check failed");
+    if (ovf) return fail(c, HYTG_ERR_OVERFLOW, "an SSSP distance does not fit in 32 bits");
+    return HYTG_OK;
+}
+
+hytg_status hytg_serve_end(hytg_ctx *c) {
+    if (!c) return HYTG_ERR_ARG;
+    if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    CK(cudaStreamSynchronize(c->s_main));
+    c->serving = false;
+    c->batch_mode = kBatchNone;
+    c->serve_busy = 0;
+    return HYTG_OK;
 }
 
 hytg_status hytg_fetch_result(hytg_ctx *c, void *out, uint64_t out_bytes) {

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
         }
         sum->pending = *pa.pending;
         sum->pending_min = ~(unsigned int)(*pa.pending_inv);
+        sum->alive = pa.alive ? *pa.alive : 0ull;
     }
 }
 

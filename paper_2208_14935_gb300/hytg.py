@@ -98,6 +98,11 @@ def load(path: Optional[str] = None):
             "hytg_hub_order": [u64, vp, vp, dbl, vp, P(u64)],
             "hytg_get_permutation": [vp, vp, u64],
             "hytg_probe_atomics": [vp, u64, u32, P(dbl), P(dbl)],
+            "hytg_serve_begin": [vp, i32, u32],
+            "hytg_serve_admit": [vp, u32, u32],
+            "hytg_serve_step": [vp, P(u64), P(u64)],
+            "hytg_serve_fetch": [vp, u32, vp, u64],
+            "hytg_serve_end": [vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -250,6 +255,30 @@ def hytg_probe_atomics(ctx, n: int = 1 << 28, reps: int = 5):
     a, b = dbl(), dbl()
     _check(ctx, load().hytg_probe_atomics(ctx, int(n), reps, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def hytg_serve_begin(ctx, algo: int, n_slots: int):
+    _check(ctx, load().hytg_serve_begin(ctx, int(algo), int(n_slots)))
+
+
+def hytg_serve_admit(ctx, slot: int, source: int):
+    _check(ctx, load().hytg_serve_admit(ctx, int(slot), int(source)))
+
+
+def hytg_serve_step(ctx):
+    fin, busy = u64(), u64()
+    _check(ctx, load().hytg_serve_step(ctx, ctypes.byref(fin), ctypes.byref(busy)))
+    return fin.value, busy.value
+
+
+def hytg_serve_fetch(ctx, slot: int, V: int, algo: int) -> np.ndarray:
+    out = np.empty(V, dtype=np.float32 if algo == HYTG_PPR else np.uint32)
+    _check(ctx, load().hytg_serve_fetch(ctx, int(slot), _ptr(out), out.nbytes))
+    return out
+
+
+def hytg_serve_end(ctx):
+    _check(ctx, load().hytg_serve_end(ctx))
 
 
 def hytg_get_iterations(ctx):

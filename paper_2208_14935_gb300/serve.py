@@ -1,0 +1,186 @@
+"""Continuous-batching query server over the hytg serving ABI.
+
+One engine (hytg context with its own copy of the graph) per algorithm;
+each engine runs one batched run whose slots hold queries.  The loop admits
+arrived queries into free slots at iteration boundaries, steps every engine
+that has busy slots (one iteration each, interleaved, so the engines' device
+work overlaps), and retires converged queries.  Admission is bounded by the
+slots, i.e. by the per-query device state each engine holds (64 BFS/SSSP
+sources or 32 PPR seeds).
+
+`python -m paper_2208_14935_gb300.serve` runs the serving benchmark on a
+synthetic graph and prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import json
+import os
+import sys
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import hytg
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    algo: str               # "bfs", "sssp" or "ppr"
+    source: int
+    admitted: float = -1.0
+    done: float = -1.0
+    result: Optional[np.ndarray] = None
+
+
+@dataclass
+class _Lane:
+    eng: "hytg.Engine"
+    algo: str
+    slots: int
+    occupant: List[Optional[Request]] = field(default_factory=list)
+    waiting: collections.deque = field(default_factory=collections.deque)
+    steps: int = 0
+
+
+class Server:
+    """Serve BFS/SSSP/PPR queries with continuous batching."""
+
+    def __init__(self, engines: Dict[str, "hytg.Engine"], slots: Optional[Dict[str, int]] = None,
+                 keep_results: bool = True):
+        self.lanes: Dict[str, _Lane] = {}
+        self.keep_results = keep_results
+        for algo, eng in engines.items():
+            n = (slots or {}).get(algo, 32 if algo == "ppr" else 64)
+            lane = _Lane(eng, algo, n, [None] * n)
+            self.lanes[algo] = lane
+
+    def run(self, requests: List[Request], clock=time.perf_counter) -> List[Request]:
+        for lane in self.lanes.values():
+            hytg.hytg_serve_begin(lane.eng.ctx, hytg.ALGOS[lane.algo], lane.slots)
+        todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        t0 = clock()
+        done: List[Request] = []
+        try:
+            while todo or any(l.waiting or any(l.occupant) for l in self.lanes.values()):
+                now = clock() - t0
+                while todo and todo[0].arrival <= now:
+                    r = todo.popleft()
+                    self.lanes[r.algo].waiting.append(r)
+                busy = False
+                for lane in self.lanes.values():
+                    for s in range(lane.slots):
+                        if lane.occupant[s] is None and lane.waiting:
+                            r = lane.waiting.popleft()
+                            hytg.hytg_serve_admit(lane.eng.ctx, s, r.source)
+                            r.admitted = clock() - t0
+                            lane.occupant[s] = r
+                    if any(lane.occupant):
+                        busy = True
+                        fin, _ = hytg.hytg_serve_step(lane.eng.ctx)
+                        lane.steps += 1
+                        s = 0
+                        while fin:
+                            if fin & 1:
+                                r = lane.occupant[s]
+                                res = hytg.hytg_serve_fetch(lane.eng.ctx, s, lane.eng.V,
+                                                            hytg.ALGOS[lane.algo])
+                                r.done = clock() - t0
+                                if self.keep_results:
+                                    r.result = res
+                                lane.occupant[s] = None
+                                done.append(r)
+                            fin >>= 1
+                            s += 1
+                if not busy and todo:
+                    wait = todo[0].arrival - (clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+        finally:
+            for lane in self.lanes.values():
+                hytg.hytg_serve_end(lane.eng.ctx)
+        return done
+
+
+def latency_stats(done: List[Request]) -> Dict[str, float]:
+    lat = np.array([r.done - r.arrival for r in done])
+    span = max(r.done for r in done) - min(r.arrival for r in done)
+    return {"n": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "qps": len(done) / span if span > 0 else float("nan")}
+
+
+def poisson_requests(n: int, rate: float, sources: Dict[str, np.ndarray], mix=(("bfs", 2), ("sssp", 2), ("ppr", 1)),
+                     seed: int = 1) -> List[Request]:
+    """n requests with exponential inter-arrival times (Poisson process of the
+    given rate, queries/s), algorithms drawn in the ratio `mix`, sources drawn
+    from `sources[algo]`; rate = inf gives a burst at t = 0."""
+    rng = np.random.default_rng(seed)
+    algos = [a for a, w in mix for _ in range(w)]
+    t = 0.0
+    out = []
+    for i in range(n):
+        if np.isfinite(rate):
+            t += rng.exponential(1.0 / rate)
+        a = algos[rng.integers(len(algos))]
+        out.append(Request(i, t, a, int(rng.choice(sources[a]))))
+    return out
+
+
+def _main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--graph", default="chunglu", choices=["chunglu", "rmat"])
+    ap.add_argument("--log2v", type=int, default=26)
+    ap.add_argument("--log2e", type=int, default=31)
+    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--n", type=int, default=200, help="requests per rate")
+    ap.add_argument("--rates", default="0.25,0.5,0.9", help="fractions of the saturation rate")
+    args = ap.parse_args()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    from gen import graphgen as gg
+    from . import build as bld
+    bld.build()
+    t = time.perf_counter()
+    if args.graph == "chunglu":
+        g = gg.chung_lu(1 << args.log2v, 1 << args.log2e, beta=2.1, wmax=255, seed=1)
+    else:
+        g = gg.rmat(args.log2v, edge_factor=1 << (args.log2e - args.log2v), seed=1)
+    gen_s = time.perf_counter() - t
+    budget = int(args.budget_gb * 1e9)
+    engines = {}
+    unweighted = gg.CSR(g.V, g.E, g.off, g.dst, None, g.name)
+    for algo in ("bfs", "sssp", "ppr"):
+        e = hytg.Engine(params={"part_bytes": 4 * 1024 * 1024})
+        e.load(g if algo == "sssp" else unweighted)
+        e.set_budget(budget)
+        engines[algo] = e
+    cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
+    rng = np.random.default_rng(3)
+    pools = {a: rng.choice(cand, 4096, replace=True) for a in ("bfs", "sssp", "ppr")}
+    srv = Server(engines, keep_results=False)
+    # saturation: every request present at t = 0 (closed burst)
+    warm = poisson_requests(min(64, args.n), float("inf"), pools, seed=9)
+    srv.run(warm)
+    sat_reqs = poisson_requests(args.n, float("inf"), pools, seed=10)
+    sat = latency_stats(srv.run(sat_reqs))
+    out = {"metric": "served queries: p50/p99 latency and queries/s (continuous batching)",
+           "graph": {"family": args.graph, "V": g.V, "E": g.E, "gen_s": round(gen_s, 1)},
+           "budget_bytes": budget, "mix": "BFS:SSSP:PPR = 2:2:1", "slots": {"bfs": 64, "sssp": 64, "ppr": 32},
+           "saturation": sat, "rates": {}}
+    for frac in [float(x) for x in args.rates.split(",")]:
+        rate = frac * sat["qps"]
+        reqs = poisson_requests(args.n, rate, pools, seed=int(frac * 1000))
+        out["rates"][f"{frac:g}x"] = {"offered_qps": rate, **latency_stats(srv.run(reqs))}
+    print(json.dumps(out), flush=True)
+    for e in engines.values():
+        e.close()
+
+
+if __name__ == "__main__":
+    _main()
