@@ -93,6 +93,9 @@ typedef struct hytg_stats {
                                          for that source; else edges_relaxed */
     uint32_t n_sources;               /* sources of the run (1 unless batched) */
     uint32_t pad_;
+    uint64_t extra_edges;             /* edges relaxed by second passes over resident
+                                         partitions ("two_pass", Sec. VI-A); not in
+                                         edges_relaxed */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -152,7 +155,11 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
  * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),
  * "hub_replicas" (how many of the first hub ids get per-SM PageRank
- * accumulators, applied at the next load; default 4096).
+ * accumulators, applied at the next load; default 4096), "sssp_delta"
+ * (delta-stepping bucket width for SSSP: -1 automatic, 0 off), "two_pass"
+ * (after relaxing a resident F task or the cache, process once more the
+ * vertices of that range that became active again, Sec. VI-A: 0 off,
+ * 1 PageRank/PPR only (default), 2 every algorithm).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);

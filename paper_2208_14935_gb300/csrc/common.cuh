@@ -181,6 +181,11 @@ struct RelaxTask {
 
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
                          const RelaxTask &t, int grid_cap, cudaStream_t s);
+cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *off,
+                               const unsigned int *dst, const unsigned int *w, long long shift,
+                               unsigned long long src_len, unsigned long long vlo,
+                               unsigned long long vhi, unsigned long long *edges_out,
+                               unsigned int *err, cudaStream_t s);
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
                           cudaStream_t s);

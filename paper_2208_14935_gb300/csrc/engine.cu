@@ -94,6 +94,7 @@ struct hytg_ctx {
     unsigned long long *d_src_work = nullptr;
     double *d_bsums = nullptr;
     unsigned long long *d_alive = nullptr;
+    unsigned long long *d_extra = nullptr;               // second-pass edge counter
     // serving (continuous batching over the batched state)
     bool serving = false;
     int serve_algo = -1;
@@ -144,6 +145,7 @@ struct hytg_ctx {
     double hub_frac = 0.08;                              // Sec. VI-A: top 8 % of vertices
     double hub_replicas = 4096;                          // hub ids with per-SM accumulators
     double sssp_delta = -1;                              // bucket width; -1 auto, 0 off
+    double two_pass = 1;                                 // Sec. VI-A second pass: 0, 1 (PageRank), 2 (all)
     uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
@@ -481,6 +483,12 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     return st;
 }
 
+// "two_pass": 0 off, 1 PageRank/PPR only (default), 2 every algorithm.
+bool second_pass_on(const hytg_ctx *c, int algo) {
+    if (c->batch_mode != kBatchNone || c->two_pass == 0) return false;
+    return c->two_pass == 2 || algo == kPR || algo == kPPR;
+}
+
 cudaError_t relax_any(hytg_ctx *c, const AlgoState &st, const ListArrays &la, const Summary *sum,
                       const RelaxTask &t, int cap, cudaStream_t s) {
     if (c->batch_mode != kBatchNone)
@@ -567,6 +575,10 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
         t.shift = 0; t.device_sized = true; t.src_len = c->carve.cache_edges;
         ScopedTime tm(c, HYTG_K_RELAX_CACHE, c->s_main);
         CK(relax_any(c, st, la, sum, t, cap, c->s_main));
+        if (second_pass_on(c, algo))
+            CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
+                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
+                                  c->d_err, c->s_main));
     }
     {
         RelaxTask t{};
@@ -654,6 +666,9 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         {
             ScopedTime tm(c, HYTG_K_RELAX_F, fs);
             CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
+            if (second_pass_on(c, algo))
+                CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
+                                      edges, c->part_vb[i], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
         }
         f_bytes += edges * ebytes;
         ++n_tasks;
@@ -755,6 +770,7 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_src_work, sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_bsums, 64 * sizeof(double)));
     ck(cudaMalloc(&c->d_alive, sizeof(unsigned long long)));
+    ck(cudaMalloc(&c->d_extra, sizeof(unsigned long long)));
     if (s != HYTG_OK) { hytg_destroy(c); return s; }
     *out = c;
     return HYTG_OK;
@@ -773,6 +789,7 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_src_work);
     dfree(c->d_bsums);
     dfree(c->d_alive);
+    dfree(c->d_extra);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < kMaxStreams; ++i) {
         if (c->s_f[i]) cudaStreamDestroy(c->s_f[i]);
@@ -963,6 +980,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
     else if (k == "hub_frac") { if (v < 0 || v > 1) return bad(); c->hub_frac = v; }
     else if (k == "sssp_delta") { if (!(v == -1 || v >= 0) || v != std::floor(v) || v > 4e9) return bad(); c->sssp_delta = v; }
+    else if (k == "two_pass") { if (v != 0 && v != 1 && v != 2) return bad(); c->two_pass = v; }
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
@@ -989,6 +1007,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "timing") *v = c->timing;
     else if (k == "hub_frac") *v = c->hub_frac;
     else if (k == "sssp_delta") *v = c->sssp_delta;
+    else if (k == "two_pass") *v = c->two_pass;
     else if (k == "hub_replicas") *v = c->hub_replicas;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
@@ -1048,6 +1067,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             delta = c->sssp_delta < 0 ? c->auto_delta : (uint64_t)c->sssp_delta;
         unsigned int bucket = delta ? (unsigned int)std::min<uint64_t>(delta, 0xFFFFFFFEull) : 0xFFFFFFFFu;
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
+        CK(cudaMemsetAsync(c->d_extra, 0, 8, c->s_main));
         if ((algo == kPR || algo == kPPR) && c->d_hub_rep && c->batch_mode == kBatchNone)
             CK(cudaMemsetAsync(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4, c->s_main));
         {
@@ -1111,7 +1131,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         CK(cudaMemcpyAsync(&ierr, c->d_err, 4, cudaMemcpyDeviceToHost, c->s_main));
         if ((algo == kPR || algo == kPPR) && c->batch_mode == kBatchNone)
             CK(cudaMemcpyAsync(prs, c->d_prsums, 16, cudaMemcpyDeviceToHost, c->s_main));
-        unsigned long long swork = 0;
+        unsigned long long swork = 0, extra = 0;
+        CK(cudaMemcpyAsync(&extra, c->d_extra, 8, cudaMemcpyDeviceToHost, c->s_main));
         if (c->batch_mode != kBatchNone)
             CK(cudaMemcpyAsync(&swork, c->d_src_work, 8, cudaMemcpyDeviceToHost, c->s_main));
         CK(cudaEventRecord(c->ev_run[1], c->s_main));
@@ -1127,6 +1148,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats.pr_rank_sum = prs[0];
         c->stats.pr_residual_sum = prs[1];
         c->stats.n_sources = c->batch_K;
+        c->stats.extra_edges = extra;
         c->stats.source_edges = c->batch_mode != kBatchNone ? swork : c->stats.edges_relaxed;
         for (size_t i = 0; i + 1 < c->iter_ev.size() && i < c->iters.size(); ++i) {
             float ms = 0;

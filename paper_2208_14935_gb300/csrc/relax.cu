@@ -137,7 +137,105 @@ __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Sum
     }
 }
 
+// Second pass over a resident vertex range (Sec. VI-A: a loaded subgraph is
+// processed once more).  Vertices of [vlo, vhi) that became active again
+// during this iteration (PageRank: delta > eps; others: frontier bit set and,
+// for bucketed SSSP, dist below the bucket) are taken and pushed along their
+// edges in `dst`/`w`, which hold CSR edges [shift, shift + src_len).
+// A lane owns a vertex of up to 32 edges; a warp shares the edges of a vertex
+// with up to kSecondPassMaxDeg; larger vertices stay active for the next
+// iteration's load-balanced relax.
+constexpr unsigned long long kSecondPassMaxDeg = 4096;
+
+template <int ALGO>
+__device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned long long v,
+                                                 unsigned long long deg, unsigned int &pay) {
+    if (ALGO == kPR || ALGO == kPPR) {
+        if (__ldcg(&st.delta[v]) <= st.eps) return false;
+        const float dl = atomicExch(&st.delta[v], 0.0f);
+        st.rank[v] += dl;
+        if (deg == 0) return false;
+        pay = __float_as_uint(st.damping * dl / (float)deg);
+        return true;
+    } else {
+        const unsigned int mask = 1u << (v & 31);
+        if (!(__ldcg(&st.bm_cur[v >> 5]) & mask)) return false;
+        if (st.bucket_limit != 0xFFFFFFFFu && __ldcg(&st.val[v]) >= st.bucket_limit) return false;
+        const unsigned int old = atomicAnd(&st.bm_cur[v >> 5], ~mask);
+        if (!(old & mask)) return false;
+        pay = __ldcg(&st.val[v]);
+        return true;
+    }
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigned long long *off,
+                                                     const unsigned int *dst, const unsigned int *w,
+                                                     long long shift, unsigned long long src_len,
+                                                     unsigned long long vlo, unsigned long long vhi,
+                                                     unsigned long long *edges_out, unsigned int *err) {
+    float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
+    const int lane = threadIdx.x & 31;
+    unsigned long long done = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long first = vlo + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull);
+    for (unsigned long long base = first; base < vhi; base += stride) {
+        const unsigned long long v = base + lane;
+        unsigned long long e0 = 0, deg = 0;
+        unsigned int pay = 0;
+        bool mine = false;
+        if (v < vhi) {
+            e0 = off[v];
+            deg = off[v + 1] - e0;
+            if (deg <= kSecondPassMaxDeg) mine = second_pass_take<ALGO>(st, v, deg, pay);
+        }
+        // lane-owned small lists
+        if (mine && deg <= 32) {
+            for (unsigned long long k = 0; k < deg; ++k) {
+                const long long i = (long long)(e0 + k) - shift;
+                if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
+                relax_edge<ALGO>(st, __ldg(dst + i), pay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
+            }
+            done += deg;
+        }
+        // warp-shared medium lists
+        unsigned int coop = __ballot_sync(0xffffffffu, mine && deg > 32);
+        while (coop) {
+            const int src = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const unsigned long long ce0 = __shfl_sync(0xffffffffu, e0, src);
+            const unsigned long long cdeg = __shfl_sync(0xffffffffu, deg, src);
+            const unsigned int cpay = __shfl_sync(0xffffffffu, pay, src);
+            for (unsigned long long k = lane; k < cdeg; k += 32) {
+                const long long i = (long long)(ce0 + k) - shift;
+                if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
+                relax_edge<ALGO>(st, __ldg(dst + i), cpay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
+            }
+            if (lane == 0) done += cdeg;
+        }
+    }
+    done = warp_sum_u64(done);
+    if (lane == 0 && done) atomicAdd(edges_out, done);
+}
+
 }  // namespace
+
+cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *off,
+                               const unsigned int *dst, const unsigned int *w, long long shift,
+                               unsigned long long src_len, unsigned long long vlo,
+                               unsigned long long vhi, unsigned long long *edges_out,
+                               unsigned int *err, cudaStream_t s) {
+    if (vhi <= vlo) return cudaSuccess;
+    unsigned long long blocks = (vhi - vlo + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    switch (st.algo) {
+        case kBFS: k_second_pass<kBFS><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
+        case kSSSP: k_second_pass<kSSSP><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
+        case kCC: k_second_pass<kCC><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
+        default: k_second_pass<kPR><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
                          const RelaxTask &t, int grid_cap, cudaStream_t s) {

@@ -323,3 +323,25 @@ def test_probes(hy):
     uni, skew = e.probe_atomics(1 << 22, 2)
     assert uni > 1 and skew > 0.1
     e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "cc", "pagerank", "ppr"])
+@pytest.mark.parametrize("force", [-1, 2, 5])
+def test_two_pass(hy, rmat16, rmat16_sym, algo, force):
+    """Second pass over resident partitions (Sec. VI-A) leaves results unchanged."""
+    g = rmat16_sym if algo == "cc" else rmat16
+    e = engine(hy, g, edge_bytes(g, algo) // 4, two_pass=2, force_route=force, seed=3)
+    src = {"bfs": 0, "sssp": 0, "ppr": 5}.get(algo)
+    check(g, algo, e.run(algo, src), 0 if src is None else src)
+    if force == 2 and algo != "ppr":
+        assert e.stats()["extra_edges"] > 0
+    e.close()
+
+
+def test_two_pass_mesh_buckets(hy):
+    g = gg.mesh(300, 200, shortcut_frac=0.001, radius=16, wmax=1000)
+    e = engine(hy, g, g.E * 8 // 5, part_bytes=16384, two_pass=2)
+    check(g, "sssp", e.run("sssp", 0))
+    check(g, "bfs", e.run("bfs", 0))
+    check(g, "cc", e.run("cc"))
+    e.close()
