@@ -96,6 +96,8 @@ typedef struct hytg_stats {
     uint64_t extra_edges;             /* edges relaxed by second passes over resident
                                          partitions ("two_pass", Sec. VI-A); not in
                                          edges_relaxed */
+    double host_compact_ms;           /* host wall time spent compacting the C route on
+                                         host threads ("compact_host" > 0), else 0 */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -159,7 +161,16 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * (delta-stepping bucket width for SSSP: -1 automatic, 0 off), "two_pass"
  * (after relaxing a resident F task or the cache, process once more the
  * vertices of that range that became active again, Sec. VI-A: 0 off,
- * 1 PageRank/PPR only (default), 2 every algorithm).
+ * 1 PageRank/PPR only (default), 2 every algorithm), "compact_host"
+ * (0: the C route's active lists are gathered by a GPU kernel over mapped
+ * host memory (default); n in 1..256: n host threads compact them into a
+ * pinned staging chunk that one explicit copy moves to the device, the
+ * CPU-compaction form of ExpTM-C of Sec. III-B; pinned staging of twice the
+ * compaction buffer is allocated outside the device budget), "priority"
+ * (Sec. VI-A delta-driven priority: 1 (default) issues the F tasks of a
+ * PageRank/PPR iteration in decreasing order of the pending |delta| their
+ * partitions hold, 0 in partition order; other algorithms always use
+ * partition order, which hub sorting makes hub-first).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);

@@ -65,6 +65,7 @@ struct PartArrays {
     unsigned long long *cursor;     // fill cursor: entries (low 24 bits) | edges << 24
     unsigned long long *pending;    // bucketed SSSP: pending vertex count
     unsigned long long *pending_inv;// bucketed SSSP: max of ~dist over pending vertices
+    unsigned long long *prio;       // delta-first order: sum over A_i of |delta| * 2^24 (PageRank)
     unsigned char *route;           // hytg_route
     const unsigned long long *alive;// batched: source mask of the frontier (or nullptr)
 };
@@ -138,6 +139,7 @@ struct AlgoState {
     float *hub_rep;
     unsigned int n_hub_rep;
     unsigned int bucket_limit;  // SSSP delta-stepping: only dist < limit is eligible (~0u: off)
+    int prio;                   // PageRank/PPR: k_count sums |delta| per partition (delta-first order)
     // batched runs (BatchMode): k_bin takes the per-source frontier word as payload
     int batch_mode;
     const unsigned long long *b_fr;   // BFS/SSSP: 64-bit source mask per vertex

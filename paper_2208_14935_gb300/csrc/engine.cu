@@ -22,7 +22,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <condition_variable>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -40,6 +42,66 @@ constexpr int kMaxStreams = 8;
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;
+};
+
+// One F task after combination: partitions [i, j], their edges, and the
+// pending delta they hold (delta-first order).
+struct FTask {
+    uint32_t i, j;
+    uint64_t edges, prio;
+};
+
+// Persistent host worker threads for the host-compaction variant of the C
+// route: run(fn) calls fn(t) once for every t in [0, size()), t = 0 on the
+// calling thread, and returns when all calls have returned.
+class HostPool {
+public:
+    explicit HostPool(unsigned n) {
+        for (unsigned i = 1; i < n; ++i) th_.emplace_back([this, i] { loop(i); });
+    }
+    ~HostPool() {
+        { std::lock_guard<std::mutex> l(mu_); stop_ = true; }
+        go_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    unsigned size() const { return (unsigned)th_.size() + 1; }
+    void run(const std::function<void(unsigned)> &fn) {
+        {
+            std::lock_guard<std::mutex> l(mu_);
+            job_ = &fn;
+            left_ = (unsigned)th_.size();
+            ++gen_;
+        }
+        go_.notify_all();
+        fn(0);
+        std::unique_lock<std::mutex> l(mu_);
+        done_.wait(l, [&] { return left_ == 0; });
+    }
+
+private:
+    void loop(unsigned id) {
+        uint64_t seen = 0;
+        for (;;) {
+            const std::function<void(unsigned)> *f;
+            {
+                std::unique_lock<std::mutex> l(mu_);
+                go_.wait(l, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                f = job_;
+            }
+            (*f)(id);
+            std::lock_guard<std::mutex> l(mu_);
+            if (--left_ == 0) done_.notify_one();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable go_, done_;
+    const std::function<void(unsigned)> *job_ = nullptr;
+    uint64_t gen_ = 0;
+    unsigned left_ = 0;
+    bool stop_ = false;
 };
 
 struct Carve {
@@ -146,6 +208,8 @@ struct hytg_ctx {
     double hub_replicas = 4096;                          // hub ids with per-SM accumulators
     double sssp_delta = -1;                              // bucket width; -1 auto, 0 off
     double two_pass = 1;                                 // Sec. VI-A second pass: 0, 1 (PageRank), 2 (all)
+    double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
+    double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
@@ -154,9 +218,18 @@ struct hytg_ctx {
     hytg_stats stats{};
     std::vector<hytg_iter_record> iters;
     std::vector<TimedLaunch> timed;
+    std::vector<FTask> f_tasks_buf;
     std::vector<cudaEvent_t> iter_ev;                    // per-iteration marks (timing on)
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
+
+    // host compaction of the C route (ExpTM-C as a CPU gather)
+    HostPool *pool = nullptr;
+    uint32_t *h_cstage[2] = {};                          // pinned: dst chunk, then w chunk
+    uint64_t h_cstage_edges = 0;
+    unsigned long long *h_clist = nullptr;               // pinned: soff[cap], then ebase[cap]
+    uint64_t h_clist_cap = 0;
+    cudaEvent_t ev_cstage[2] = {}, ev_clist = nullptr;
 };
 
 namespace {
@@ -230,7 +303,7 @@ void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &
 // [n_act, pend_inv] is zeroed before every count; the whole buffer is copied
 // to the host once per iteration.
 struct SumLayout {
-    size_t n_act, entries, edges, lines, cursor, pending, pend_inv, zero_end, route_entry,
+    size_t n_act, entries, edges, lines, cursor, prio, pending, pend_inv, zero_end, route_entry,
         route_edge, route, host_end, total;
 };
 SumLayout sum_layout(uint32_t N) {
@@ -242,6 +315,7 @@ SumLayout sum_layout(uint32_t N) {
     L.edges = o; o += a;
     L.lines = o; o += a;
     L.cursor = o; o += a;
+    L.prio = o; o += a;
     L.pending = o; o += 8;
     L.pend_inv = o; o += 8;
     L.zero_end = o;
@@ -267,6 +341,7 @@ PartArrays part_arrays(hytg_ctx *c) {
     pa.cursor = (unsigned long long *)(b + L.cursor);
     pa.pending = (unsigned long long *)(b + L.pending);
     pa.pending_inv = (unsigned long long *)(b + L.pend_inv);
+    pa.prio = (unsigned long long *)(b + L.prio);
     pa.alive = c->batch_mode != kBatchNone ? c->d_alive : nullptr;
     return pa;
 }
@@ -401,8 +476,8 @@ struct ScopedTime {
     int kind;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
-    ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
-        c->stats.kernel_launches += (kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
+    ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_, bool kernel = true) : c(c_), kind(kind_), s(s_) {
+        c->stats.kernel_launches += (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
         if (c->timing != 0) {
             a = pool_event(c);
             cudaEventRecord(a, s);
@@ -480,6 +555,7 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     const bool pr = (algo == kPR || algo == kPPR);
     st.hub_rep = pr ? c->d_hub_rep : nullptr;
     st.n_hub_rep = pr && c->d_hub_rep ? c->n_hub_rep : 0;
+    st.prio = pr && c->priority != 0 && c->batch_mode == kBatchNone;
     return st;
 }
 
@@ -606,6 +682,107 @@ hytg_status ensure_cache(hytg_ctx *c, int n_arrays) {
     return HYTG_OK;
 }
 
+// The C route with the compaction done by host threads (the CPU-compaction
+// form of ExpTM-C, Sec. III-B / Sec. V): the route's active list (row offset
+// and route edge base per entry) comes back to the host, the worker threads
+// copy each entry's edges from the pinned CSR into a pinned staging chunk at
+// its route position, one explicit copy moves the chunk into the compaction
+// buffer and the compact-mode relax runs on it.  Two staging chunks let the
+// threads fill one while the other is copied and relaxed.
+hytg_status host_compact(hytg_ctx *c, int algo, unsigned int bucket, const Summary *hs, int n_arrays) {
+    Carve &cv = c->carve;
+    const uint64_t nC = hs->route_entries[kRouteC];
+    const uint64_t base = hs->route_entry_base[kRouteC];
+    const uint64_t c_edges = hs->route_edges[kRouteC];
+    const unsigned nt = (unsigned)c->compact_host;
+    if (!c->pool || c->pool->size() != nt) {
+        delete c->pool;
+        c->pool = nullptr;
+        c->pool = new HostPool(nt);
+    }
+    if (c->h_cstage_edges != cv.compact_edges) {
+        for (int b = 0; b < 2; ++b) {
+            if (c->h_cstage[b]) CK(cudaFreeHost(c->h_cstage[b]));
+            c->h_cstage[b] = nullptr;
+        }
+        c->h_cstage_edges = 0;
+        for (int b = 0; b < 2; ++b)
+            if (cudaHostAlloc((void **)&c->h_cstage[b], cv.compact_edges * 8, cudaHostAllocDefault) != cudaSuccess)
+                return fail(c, HYTG_ERR_HOSTMEM, "pinned staging for host compaction");
+        c->h_cstage_edges = cv.compact_edges;
+    }
+    if (c->h_clist_cap < nC) {
+        if (c->h_clist) CK(cudaFreeHost(c->h_clist));
+        c->h_clist = nullptr;
+        c->h_clist_cap = 0;
+        uint64_t cap = 1024;
+        while (cap < nC) cap *= 2;
+        if (cudaHostAlloc((void **)&c->h_clist, cap * 16, cudaHostAllocDefault) != cudaSuccess)
+            return fail(c, HYTG_ERR_HOSTMEM, "pinned list buffer for host compaction");
+        c->h_clist_cap = cap;
+    }
+    unsigned long long *h_soff = c->h_clist, *h_ebase = c->h_clist + c->h_clist_cap;
+    CK(cudaStreamWaitEvent(c->s_c, c->ev_bin, 0));
+    CK(cudaMemcpyAsync(h_soff, c->d_soff + base, nC * 8, cudaMemcpyDeviceToHost, c->s_c));
+    CK(cudaMemcpyAsync(h_ebase, c->d_ebase + base, nC * 8, cudaMemcpyDeviceToHost, c->s_c));
+    CK(cudaEventRecord(c->ev_clist, c->s_c));
+    CK(cudaEventSynchronize(c->ev_clist));
+    const auto t0 = std::chrono::steady_clock::now();
+    AlgoState st = algo_state(c, algo, bucket);
+    ListArrays la = list_arrays(c);
+    Summary *dsum = (Summary *)c->d_sumbuf;
+    const uint32_t *hd = c->h_dst, *hw = c->h_w;
+    const uint64_t E = c->E;
+    std::atomic<int> bad{0};
+    int chunk = 0;
+    for (uint64_t cb = 0; cb < c_edges; cb += cv.compact_edges, ++chunk) {
+        const uint64_t ce = std::min<uint64_t>(c_edges, cb + cv.compact_edges);
+        const int b = chunk & 1;
+        if (chunk >= 2) CK(cudaEventSynchronize(c->ev_cstage[b]));   // its copy two chunks ago
+        uint32_t *sd = c->h_cstage[b], *sw = c->h_cstage[b] + cv.compact_edges;
+        const std::function<void(unsigned)> job = [&](unsigned t) {
+            // route edges [a, z) of this chunk, split evenly across the threads
+            const uint64_t a = cb + (ce - cb) * t / nt, z = cb + (ce - cb) * (t + 1) / nt;
+            if (a >= z) return;
+            uint64_t i = (uint64_t)(std::upper_bound(h_ebase, h_ebase + nC, (unsigned long long)a) - h_ebase);
+            if (i == 0) { bad = 1; return; }
+            --i;
+            for (uint64_t pos = a; pos < z; ++i) {
+                if (i >= nC) { bad = 1; return; }
+                const uint64_t e_hi = i + 1 < nC ? h_ebase[i + 1] : c_edges;
+                const uint64_t take = std::min<uint64_t>(e_hi, z) - pos;
+                const uint64_t src = h_soff[i] + (pos - h_ebase[i]);
+                if (e_hi <= pos || src + take > E) { bad = 1; return; }
+                std::memcpy(sd + (pos - cb), hd + src, take * 4);
+                if (n_arrays == 2) std::memcpy(sw + (pos - cb), hw + src, take * 4);
+                pos += take;
+            }
+        };
+        c->pool->run(job);
+        if (bad) return fail(c, HYTG_ERR_CUDA, "host compaction: active list out of range");
+        {
+            ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c, false);
+            CK(cudaMemcpyAsync(cv.cmp_dst, sd, (ce - cb) * 4, cudaMemcpyHostToDevice, c->s_c));
+            if (n_arrays == 2)
+                CK(cudaMemcpyAsync(cv.cmp_w, sw, (ce - cb) * 4, cudaMemcpyHostToDevice, c->s_c));
+        }
+        CK(cudaEventRecord(c->ev_cstage[b], c->s_c));
+        RelaxTask r{};
+        r.route = kRouteC; r.mode = kModeCompact; r.dst = cv.cmp_dst; r.w = cv.cmp_w;
+        r.shift = (long long)cb; r.k_begin = cb; r.k_end = ce; r.first_entry = 0;
+        r.device_sized = false;
+        r.src_len = ce - cb;
+        {
+            ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
+            CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
+        }
+    }
+    c->stats.host_compact_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    CK(cudaEventRecord(c->ev_c, c->s_c));
+    CK(cudaStreamWaitEvent(c->s_main, c->ev_c, 0));
+    return HYTG_OK;
+}
+
 // Issue one iteration's route work after its summary reached the host:
 // F tasks (task combination of Alg. 1, copy + relax per stream), the C
 // route in chunks of the compaction buffer, and the per-iteration statistics.
@@ -627,22 +804,40 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     ListArrays la = list_arrays(c);
     Summary *dsum = (Summary *)c->d_sumbuf;
     // --- F: task combination (Alg. 1, k consecutive partitions, slot capacity)
-    uint64_t f_bytes = 0;
-    uint32_t n_tasks = 0;
-    f_streams_used.clear();
+    std::vector<FTask> &tasks = c->f_tasks_buf;
+    tasks.clear();
+    const unsigned long long *p_prio = (const unsigned long long *)(hb + L.prio);
+    const bool by_delta = algo_state(c, algo).prio != 0;
     uint32_t i = 0;
     while (i < N) {
         if (p_route[i] != kRouteF) { ++i; continue; }
         uint32_t j = i;
         uint64_t edges = c->part_eb[i + 1] - c->part_eb[i];
+        uint64_t pr = by_delta ? p_prio[i] : 0;
         while (j + 1 < N && p_route[j + 1] == kRouteF && (j + 1 - i + 1) <= (uint32_t)c->k &&
                edges + (c->part_eb[j + 2] - c->part_eb[j + 1]) <= cv.slot_edges) {
             ++j;
             edges += c->part_eb[j + 1] - c->part_eb[j];
+            if (by_delta) pr += p_prio[j];
         }
+        tasks.push_back({i, j, edges, pr});
+        i = j + 1;
+    }
+    // delta-driven priority (Sec. VI-A): the tasks whose partitions hold the
+    // most pending delta go first; otherwise partition order, which puts the
+    // hub partitions (hub sorting) first
+    if (by_delta)
+        std::stable_sort(tasks.begin(), tasks.end(),
+                         [](const FTask &a, const FTask &b) { return a.prio > b.prio; });
+    uint64_t f_bytes = 0;
+    uint32_t n_tasks = 0;
+    f_streams_used.clear();
+    for (const FTask &ft : tasks) {
+        const uint32_t i0 = ft.i, j = ft.j;
+        const uint64_t edges = ft.edges;
         const uint32_t slot = n_tasks % cv.n_slots;
         cudaStream_t fs = c->s_f[slot];
-        const uint64_t e0 = c->part_eb[i];
+        const uint64_t e0 = c->part_eb[i0];
         {
             // the copy needs only the route decision (already on the host)
             // and the slot's previous relax (same stream), not the lists
@@ -658,9 +853,9 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         RelaxTask t{};
         t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
         t.shift = (long long)e0;
-        t.k_begin = p_redge[i];
+        t.k_begin = p_redge[i0];
         t.k_end = p_redge[j] + p_edges[j];
-        t.first_entry = p_rentry[i];
+        t.first_entry = p_rentry[i0];
         t.device_sized = false;
         t.src_len = edges;
         {
@@ -668,15 +863,17 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
             if (second_pass_on(c, algo))
                 CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
-                                      edges, c->part_vb[i], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
+                                      edges, c->part_vb[i0], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
         }
         f_bytes += edges * ebytes;
         ++n_tasks;
-        i = j + 1;
     }
     // --- C: gather active lists into the compaction buffer, relax, in chunks
     const uint64_t c_edges = hs->route_edges[kRouteC];
-    if (c_edges) {
+    if (c_edges && c->compact_host > 0) {
+        hytg_status hs_c = host_compact(c, algo, bucket, hs, n_arrays);
+        if (hs_c != HYTG_OK) return hs_c;
+    } else if (c_edges) {
         CK(cudaStreamWaitEvent(c->s_c, c->ev_bin, 0));
         for (uint64_t cb = 0; cb < c_edges; cb += cv.compact_edges) {
             const uint64_t ce = std::min<uint64_t>(c_edges, cb + cv.compact_edges);
@@ -716,7 +913,11 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         c->stats.route_edges[r] += hs->route_edges[r];
     }
     const uint64_t zb = hs->route_lines[kRouteZ] * (uint64_t)c->m;
-    const uint64_t cbts = hs->route_lines[kRouteC] * (uint64_t)c->m;
+    // host compaction moves the active lists themselves plus their index
+    // (soff, ebase) back to the host; the GPU gather reads 128-byte lines
+    const uint64_t cbts = c->compact_host > 0
+        ? hs->route_edges[kRouteC] * ebytes + hs->route_entries[kRouteC] * 16
+        : hs->route_lines[kRouteC] * (uint64_t)c->m;
     c->stats.link_bytes[kRouteF] += f_bytes;
     c->stats.link_bytes[kRouteZ] += zb;
     c->stats.link_bytes[kRouteC] += cbts;
@@ -761,6 +962,8 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     for (int i = 0; i < 2; ++i) ck(cudaEventCreateWithFlags(&c->ev_sum[i], cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&c->ev_c, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) ck(cudaEventCreateWithFlags(&c->ev_cstage[i], cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&c->ev_clist, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) ck(cudaEventCreate(&c->ev_run[i]));
     ck(cudaMalloc(&c->d_overflow, sizeof(unsigned int)));
     ck(cudaMalloc(&c->d_err, sizeof(unsigned int)));
@@ -799,6 +1002,13 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_c) cudaEventDestroy(c->ev_c);
     for (int i = 0; i < 2; ++i) if (c->ev_run[i]) cudaEventDestroy(c->ev_run[i]);
+    delete c->pool;
+    for (int i = 0; i < 2; ++i) {
+        if (c->h_cstage[i]) cudaFreeHost(c->h_cstage[i]);
+        if (c->ev_cstage[i]) cudaEventDestroy(c->ev_cstage[i]);
+    }
+    if (c->h_clist) cudaFreeHost(c->h_clist);
+    if (c->ev_clist) cudaEventDestroy(c->ev_clist);
     if (c->s_c) cudaStreamDestroy(c->s_c);
     if (c->s_main) cudaStreamDestroy(c->s_main);
     delete c;
@@ -982,6 +1192,8 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "sssp_delta") { if (!(v == -1 || v >= 0) || v != std::floor(v) || v > 4e9) return bad(); c->sssp_delta = v; }
     else if (k == "two_pass") { if (v != 0 && v != 1 && v != 2) return bad(); c->two_pass = v; }
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
+    else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
+    else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1009,6 +1221,8 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "sssp_delta") *v = c->sssp_delta;
     else if (k == "two_pass") *v = c->two_pass;
     else if (k == "hub_replicas") *v = c->hub_replicas;
+    else if (k == "compact_host") *v = c->compact_host;
+    else if (k == "priority") *v = c->priority;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }

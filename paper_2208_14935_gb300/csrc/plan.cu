@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
          rd < n_rounds; rd += nwarps) {
         unsigned int cur_p = 0xFFFFFFFFu;
         unsigned long long p_lo = 1, p_hi = 0;   // word range of cur_p
-        unsigned long long a_nact = 0, a_ent = 0, a_edges = 0, a_lines = 0;
+        unsigned long long a_nact = 0, a_ent = 0, a_edges = 0, a_lines = 0, a_prio = 0;
         const unsigned long long wbase = rd * 32;
         const unsigned int bits = st.bm_cur[wbase + lane];
         unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
@@ -72,16 +72,19 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
             unsigned int wq[kBatch];
             unsigned long long wi[kBatch], o0[kBatch], o1[kBatch];
             unsigned int dv[kBatch];
+            float dl[kBatch];
             next_batch(nz, bits, wbase, wq, wi);
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
                 o0[q] = o1[q] = 0;
                 dv[q] = 0;
+                dl[q] = 0.f;
                 if ((wq[q] >> lane) & 1u) {
                     const unsigned long long v = wi[q] * 32 + lane;
                     o0[q] = g.off[v];
                     o1[q] = g.off[v + 1];
                     if (bucketed) dv[q] = st.val[v];
+                    if (st.prio) dl[q] = st.delta[v];
                 }
             }
 #pragma unroll
@@ -102,8 +105,9 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                         atomicAdd(&pa.entries[cur_p], a_ent);
                         atomicAdd(&pa.edges[cur_p], a_edges);
                         atomicAdd(&pa.lines[cur_p], a_lines);
+                        if (st.prio) atomicAdd(&pa.prio[cur_p], a_prio);
                     }
-                    a_nact = a_ent = a_edges = a_lines = 0;
+                    a_nact = a_ent = a_edges = a_lines = a_prio = 0;
                     cur_p = find_part(g.part_wb, g.N, widx);
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
@@ -115,6 +119,12 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                 a_ent += __popc(__ballot_sync(0xffffffffu, deg > 0));
                 a_edges += warp_sum_u64(deg);
                 a_lines += warp_sum_u64(ln);
+                if (st.prio) {
+                    // |delta| in units of 2^-24, capped at 2^40 per vertex; the
+                    // sum only orders the F tasks, so rounding cannot matter
+                    const float x = fminf(fabsf(dl[q]) * 16777216.f, 1099511627776.f);
+                    a_prio += warp_sum_u64(act ? (unsigned long long)x : 0ull);
+                }
             }
         }
         if (lane == 0 && cur_p != 0xFFFFFFFFu && a_nact) {
@@ -122,6 +132,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
             atomicAdd(&pa.entries[cur_p], a_ent);
             atomicAdd(&pa.edges[cur_p], a_edges);
             atomicAdd(&pa.lines[cur_p], a_lines);
+            if (st.prio) atomicAdd(&pa.prio[cur_p], a_prio);
         }
     }
     if (bucketed) {

@@ -38,7 +38,8 @@ class hytg_stats(ctypes.Structure):
                 ("cache_fill_bytes", u64), ("f_tasks", u64), ("kernel_launches", u64),
                 ("wall_ms", dbl), ("kernel_ms", dbl * 12), ("kernel_count", u64 * 12),
                 ("pr_residual_sum", dbl), ("pr_rank_sum", dbl), ("device_ms", dbl),
-                ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64)]
+                ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64),
+                ("host_compact_ms", dbl)]
 
 
 class hytg_info(ctypes.Structure):

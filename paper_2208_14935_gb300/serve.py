@@ -140,6 +140,8 @@ def _main():
     ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--n", type=int, default=200, help="requests per rate")
     ap.add_argument("--rates", default="0.25,0.5,0.9", help="fractions of the saturation rate")
+    ap.add_argument("--max-seconds", type=float, default=60.0,
+                    help="cap on the arrival span of each rated run (fewer requests at low rates)")
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -175,7 +177,8 @@ def _main():
            "saturation": sat, "rates": {}}
     for frac in [float(x) for x in args.rates.split(",")]:
         rate = frac * sat["qps"]
-        reqs = poisson_requests(args.n, rate, pools, seed=int(frac * 1000))
+        n = max(8, min(args.n, int(rate * args.max_seconds)))
+        reqs = poisson_requests(n, rate, pools, seed=int(frac * 1000))
         out["rates"][f"{frac:g}x"] = {"offered_qps": rate, **latency_stats(srv.run(reqs))}
     print(json.dumps(out), flush=True)
     for e in engines.values():

@@ -345,3 +345,16 @@ def test_two_pass_mesh_buckets(hy):
     check(g, "bfs", e.run("bfs", 0))
     check(g, "cc", e.run("cc"))
     e.close()
+
+
+@pytest.mark.parametrize("algo", ["pagerank", "ppr"])
+@pytest.mark.parametrize("prio", [0, 1])
+@pytest.mark.parametrize("force", [-1, 2])
+def test_delta_first_order(hy, rmat16, algo, prio, force):
+    """F tasks in delta-first order (Sec. VI-A) or partition order: the same
+    fixed point within the PageRank tolerance."""
+    e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, priority=prio, force_route=force)
+    src = 5 if algo == "ppr" else None
+    check(rmat16, algo, e.run(algo, src), 5 if src is not None else 0)
+    assert e.stats()["f_tasks"] > 0
+    e.close()
