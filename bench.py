@@ -56,6 +56,9 @@ def parse():
                     help="comma-separated subset of bfs,sssp,cc,pagerank (profiling runs)")
     ap.add_argument("--no-probe", action="store_true", help="skip the host-link probe")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain runs")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="SCALE",
+                    help="only the batched workload (64 BFS/SSSP sources, 32 PPR seeds) on R-MAT "
+                         "SCALE against the same sources run one at a time; prints its own line")
     return ap.parse_args()
 
 
@@ -244,10 +247,38 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- ours ----
+def run_batched_only(args):
+    """Batched workload at its own size (R-MAT 25: 33,554,432 vertices,
+    536,870,912 edges, 25 % budget): 64 BFS and SSSP sources and 32 PPR
+    seeds per run, against the same sources one at a time."""
+    from paper_2208_14935_gb300 import build as bld
+    bld.build()
+    from paper_2208_14935_gb300 import hytg
+    from gen import graphgen as gg
+    t0 = time.perf_counter()
+    g = gg.rmat(args.batched_only, seed=1, wmax=64)
+    t_gen = time.perf_counter() - t0
+    graph_bytes = g.E * 8 + (g.V + 1) * 8
+    eng = hytg.Engine(g, budget=int(args.budget_frac * graph_bytes),
+                      params={"part_bytes": args.part_bytes})
+    res = batched_vs_plain(hytg, eng, g)
+    eng.close()
+    line = {"metric": "batched vs plain GTEPS (per-source edges relaxed / device time)",
+            "unit": "GTEPS", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"rmat{args.batched_only} batched BFS/SSSP x64, PPR x32, budget "
+                                   f"{args.budget_frac:.0%} of graph bytes",
+                       "V": g.V, "E": g.E, "budget_bytes": int(args.budget_frac * graph_bytes),
+                       "graph_gen_s": round(t_gen, 1)},
+            "batched_vs_plain": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched_only:
+        return run_batched_only(args)
     rank, world, local = dist_env()
     algos = [a for a in args.algos.split(",") if a]
     assert all(a in ALGOS for a in algos), args.algos

@@ -23,6 +23,39 @@ namespace hytg {
 namespace {
 
 constexpr int kBatch = 4;   // bitmap words whose loads are issued together
+constexpr int kPrefetch = 8;   // bitmap rounds a warp loads before scanning them
+
+// This warp's rounds of 32 bitmap words (rd = warp, warp + nwarps, ...),
+// kPrefetch at a time: the words of kPrefetch rounds are loaded together so
+// their latencies overlap, and rounds whose 32 words are all zero (most of
+// them when the frontier is small) are skipped.  body(rd, bits) sees the
+// round index and this lane's word.  The walk only reads the bitmap; body
+// may rewrite its own round's words.
+template <class F>
+__device__ __forceinline__ void for_rounds(const unsigned int *bm, unsigned long long n_rounds, F &&body) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    for (unsigned long long r0 = w; r0 < n_rounds; r0 += nwarps * kPrefetch) {
+        unsigned int pre[kPrefetch];
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) {
+            const unsigned long long rd = r0 + (unsigned long long)j * nwarps;
+            pre[j] = rd < n_rounds ? bm[rd * 32 + lane] : 0u;
+        }
+        unsigned int live = 0;
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j)
+            live |= (__any_sync(0xffffffffu, pre[j] != 0) ? 1u : 0u) << j;
+        while (live) {                              // warp-uniform
+            const int j = __ffs(live) - 1;
+            live &= live - 1;
+            // reloaded (a cache hit) rather than kept live across the body
+            const unsigned long long rd = r0 + (unsigned long long)j * nwarps;
+            body(rd, bm[rd * 32 + lane]);
+        }
+    }
+}
 
 // Partition holding bitmap word `widx` (bounds are word indices).
 __device__ __forceinline__ unsigned int find_part(const unsigned int *wb, unsigned int N,
@@ -55,18 +88,15 @@ __device__ __forceinline__ void next_batch(unsigned int &nz, unsigned int bits,
 __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArrays pa,
                                                unsigned long long m) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long n_rounds = g.n_words_alloc / 32;
     const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
     unsigned long long pend = 0;
     unsigned int pend_min = 0xFFFFFFFFu;
-    for (unsigned long long rd = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-         rd < n_rounds; rd += nwarps) {
+    for_rounds(st.bm_cur, n_rounds, [&](unsigned long long rd, unsigned int bits) {
         unsigned int cur_p = 0xFFFFFFFFu;
         unsigned long long p_lo = 1, p_hi = 0;   // word range of cur_p
         unsigned long long a_nact = 0, a_ent = 0, a_edges = 0, a_lines = 0, a_prio = 0;
         const unsigned long long wbase = rd * 32;
-        const unsigned int bits = st.bm_cur[wbase + lane];
         unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
         while (nz) {
             unsigned int wq[kBatch];
@@ -134,7 +164,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
             atomicAdd(&pa.lines[cur_p], a_lines);
             if (st.prio) atomicAdd(&pa.prio[cur_p], a_prio);
         }
-    }
+    });
     if (bucketed) {
         pend = warp_sum_u64(pend);
 #pragma unroll
@@ -249,18 +279,15 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                                              const Summary *sum) {
     const int lane = threadIdx.x & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
-    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long n_rounds = g.n_words_alloc / 32;
     const bool batched = st.batch_mode != kBatchNone;
     const bool is_pr = !batched && (st.algo == kPR || st.algo == kPPR);
     const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
     unsigned long long work = 0;
-    for (unsigned long long rd = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-         rd < n_rounds; rd += nwarps) {
+    for_rounds(st.bm_cur, n_rounds, [&](unsigned long long rd, unsigned int bits) {
         unsigned int cur_p = 0xFFFFFFFFu;
         unsigned long long p_lo = 1, p_hi = 0, rbase = 0, tbase = 0, pe0 = 0, pg0 = 0;
         const unsigned long long wbase = rd * 32;
-        const unsigned int bits = st.bm_cur[wbase + lane];
         unsigned int keep = bits;                       // bits left for a later bucket
         unsigned int nz = __ballot_sync(0xffffffffu, bits != 0);
         while (nz) {
@@ -348,7 +375,7 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
             }
         }
         if (keep != bits) st.bm_cur[wbase + lane] = keep;
-    }
+    });
     if (batched) {
         work = warp_sum_u64(work);
         if (lane == 0 && work) atomicAdd(st.src_work, work);
@@ -357,12 +384,30 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
 
 }  // namespace
 
+// Blocks of 256 threads that fit on the device at once for `kernel`.
+template <class K>
+unsigned long long resident_blocks(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
+        sms <= 0 || per_sm <= 0)
+        return 152ull * 2;
+    return (unsigned long long)sms * (unsigned long long)per_sm;
+}
+
+// Grid of a bitmap walk: one resident wave, at most one round per warp.
+unsigned long long walk_blocks(unsigned long long rounds, unsigned long long resident) {
+    unsigned long long blocks = (rounds + 7) / 8;
+    return blocks < resident ? blocks : resident;
+}
+
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
                          unsigned long long m, cudaStream_t s) {
     const unsigned long long rounds = g.n_words_alloc / 32;
     if (rounds == 0) return cudaSuccess;
-    unsigned long long blocks = (rounds + 7) / 8;
-    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    static const unsigned long long resident = resident_blocks(k_count);
+    const unsigned long long blocks = walk_blocks(rounds, resident);
     k_count<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, m);
     return cudaGetLastError();
 }
@@ -377,8 +422,8 @@ cudaError_t launch_bin(const GraphDev &g, const AlgoState &st, const PartArrays 
                        const ListArrays &la, const Summary *sum, cudaStream_t s) {
     const unsigned long long rounds = g.n_words_alloc / 32;
     if (rounds == 0) return cudaSuccess;
-    unsigned long long blocks = (rounds + 7) / 8;
-    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    static const unsigned long long resident = resident_blocks(k_bin);
+    const unsigned long long blocks = walk_blocks(rounds, resident);
     k_bin<<<(unsigned int)blocks, 256, 0, s>>>(g, st, pa, la, sum);
     return cudaGetLastError();
 }

@@ -153,7 +153,9 @@ __device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned l
     if (ALGO == kPR || ALGO == kPPR) {
         if (__ldcg(&st.delta[v]) <= st.eps) return false;
         const float dl = atomicExch(&st.delta[v], 0.0f);
-        st.rank[v] += dl;
+        // atomic: with a forced route, an F range can overlap the cache range,
+        // and the two second passes may each take a share of v's delta
+        atomicAdd(&st.rank[v], dl);
         if (deg == 0) return false;
         pay = __float_as_uint(st.damping * dl / (float)deg);
         return true;
