@@ -98,6 +98,8 @@ typedef struct hytg_stats {
                                          edges_relaxed */
     double host_compact_ms;           /* host wall time spent compacting the C route on
                                          host threads ("compact_host" > 0), else 0 */
+    uint64_t graph_launches;          /* launches of the device-loop graph ("device_loop") */
+    uint64_t graph_iterations;        /* iterations run entirely inside those launches */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -170,7 +172,12 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * (Sec. VI-A delta-driven priority: 1 (default) issues the F tasks of a
  * PageRank/PPR iteration in decreasing order of the pending |delta| their
  * partitions hold, 0 in partition order; other algorithms always use
- * partition order, which hub sorting makes hub-first).
+ * partition order, which hub sorting makes hub-first), "device_loop" (1,
+ * default: single-source runs replay one iteration (planning, binning,
+ * cache and zero-copy relax) inside a CUDA graph with a WHILE node until an
+ * iteration needs the F or C route, whose copies the host issues, or the
+ * run ends; 0: the host drives every iteration.  Iterations run in the
+ * graph report no per-iteration device time and are not in kernel_ms).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);

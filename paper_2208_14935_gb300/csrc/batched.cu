@@ -65,6 +65,7 @@ __global__ void k_b_sources(BatchState b, const unsigned int *src, unsigned int 
 // vertices so the bitmap word is written whole (the binning pass cleared it).
 __global__ void k_b_commit(BatchState b, unsigned long long V, unsigned long long n_words_alloc,
                            unsigned int level, unsigned int *bm) {
+    if (b.loop) level = b.loop->it;
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
@@ -192,6 +193,7 @@ __global__ void k_serve_extract(BatchState b, unsigned long long V, unsigned int
 __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListArrays la,
                                                              const Summary *sum, RelaxTask t) {
     __shared__ TileSmem<true> sm;
+    if (b.loop && !b.loop->work) return;
     const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
     const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
     if (kb >= ke) return;
@@ -236,6 +238,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                                                               unsigned int *bm,
                                                               unsigned int *overflow) {
     __shared__ TileSmem<true> sm;
+    if (b.loop && !b.loop->work) return;
     const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
     const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
     if (kb >= ke) return;

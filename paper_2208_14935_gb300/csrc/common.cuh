@@ -21,7 +21,7 @@ constexpr int kRelaxBlock = 256;
 constexpr int kRelaxIPT = 8;
 constexpr int kTile = kRelaxBlock * kRelaxIPT;   // 2048 edges per tile
 
-constexpr int kSelectBlock = 1024;
+constexpr int kSelectBlock = 512;    // 128 registers per thread: the per-route sums stay in registers
 
 enum Algo : int { kBFS = 0, kSSSP = 1, kCC = 2, kPR = 3, kPPR = 4 };
 
@@ -125,6 +125,25 @@ struct GraphDev {
     unsigned int N;
 };
 
+// Control block of the device-driven iteration loop (a CUDA graph whose
+// WHILE node repeats plan + cache/Z relax until an iteration needs the F or C
+// route, the frontier is empty, or the iteration cap is reached).
+enum LoopStatus : unsigned int { kLoopRun = 0, kLoopDone = 1, kLoopHost = 2, kLoopMaxIt = 3 };
+struct LoopCtl {
+    unsigned int status;            // LoopStatus when the loop exits
+    unsigned int it;                // number of the iteration being planned
+    unsigned int bucket;            // SSSP delta-stepping bucket limit (~0u: off)
+    unsigned int work;              // 1: this iteration's bin and relax run on the device
+    unsigned int n_rec, rec_cap;    // iteration records written / capacity
+    unsigned long long delta;       // bucket width (0: no buckets)
+    unsigned long long max_it;
+    unsigned long long m;           // request bytes (link bytes of zero-copy lines)
+    void *rec;                      // hytg_iter_record[rec_cap]
+    // totals over the device iterations of this launch
+    unsigned long long route_parts[kRoutes], route_entries[kRoutes], route_edges[kRoutes];
+    unsigned long long z_lines, vertices, edges, iterations;
+};
+
 struct AlgoState {
     int algo;
     unsigned int *val;       // BFS level / SSSP dist / CC label
@@ -139,6 +158,7 @@ struct AlgoState {
     float *hub_rep;
     unsigned int n_hub_rep;
     unsigned int bucket_limit;  // SSSP delta-stepping: only dist < limit is eligible (~0u: off)
+    LoopCtl *loop;              // device loop: bucket from loop->bucket; bin/relax run if loop->work
     int prio;                   // PageRank/PPR: k_count sums |delta| per partition (delta-first order)
     // batched runs (BatchMode): k_bin takes the per-source frontier word as payload
     int batch_mode;
@@ -156,6 +176,7 @@ struct BatchState {
     float *delta, *rank, *msg;            // PPR, [v * 32 + s]
     unsigned int *fr32;                   // PPR seeds taken at v this iteration
     unsigned long long *alive;            // OR of every vertex's frontier mask (serving)
+    const LoopCtl *loop;                  // device loop: level from loop->it; relax gated by loop->work
 };
 constexpr unsigned int kHubReplicas = 256;
 
@@ -210,6 +231,10 @@ cudaError_t launch_serve_extract(const BatchState &b, unsigned long long V, unsi
                                  double *sums, cudaStream_t s);
 cudaError_t launch_b_finalize(const BatchState &b, unsigned long long V, unsigned int K,
                               const unsigned int *perm, void *out, double *sums, cudaStream_t s);
+
+cudaError_t launch_zero_u64(unsigned long long *p, unsigned long long n, cudaStream_t s);
+cudaError_t launch_loop_decide(const Summary *sum, LoopCtl *ctl, unsigned long long cond_handle,
+                               cudaStream_t s);
 
 cudaError_t launch_init(const AlgoState &st, unsigned long long V, unsigned long long n_words_alloc,
                         unsigned int source, cudaStream_t s);

@@ -210,6 +210,7 @@ struct hytg_ctx {
     double two_pass = 1;                                 // Sec. VI-A second pass: 0, 1 (PageRank), 2 (all)
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
+    double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
     uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
@@ -219,7 +220,7 @@ struct hytg_ctx {
     std::vector<hytg_iter_record> iters;
     std::vector<TimedLaunch> timed;
     std::vector<FTask> f_tasks_buf;
-    std::vector<cudaEvent_t> iter_ev;                    // per-iteration marks (timing on)
+    std::vector<std::pair<size_t, cudaEvent_t>> iter_ev; // (iteration index, start mark), timing on
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
 
@@ -230,6 +231,18 @@ struct hytg_ctx {
     unsigned long long *h_clist = nullptr;               // pinned: soff[cap], then ebase[cap]
     uint64_t h_clist_cap = 0;
     cudaEvent_t ev_cstage[2] = {}, ev_clist = nullptr;
+
+    // device-driven iteration loop: a graph whose WHILE node repeats one
+    // iteration (plan, k_loop_decide, bin, cache and Z relax) on the device
+    cudaStream_t s_cap = nullptr;                        // capture stream
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    std::string loop_key;                                // what the captured body depends on
+    LoopCtl *d_loop = nullptr, *h_loop = nullptr;        // device control block, pinned mirror
+    hytg_iter_record *d_loop_rec = nullptr;
+    uint32_t loop_rec_cap = 4096;
+    uint32_t loop_kernels = 0;                           // kernels in one body iteration
+    bool capturing = false;
 };
 
 namespace {
@@ -256,7 +269,16 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+void free_loop_graph(hytg_ctx *c) {
+    if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+    if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+    c->loop_exec = nullptr;
+    c->loop_graph = nullptr;
+    c->loop_key.clear();
+}
+
 void free_graph(hytg_ctx *c) {
+    free_loop_graph(c);             // its body holds pointers into the graph's arrays
     if (c->h_dst) cudaFreeHost(c->h_dst);
     if (c->h_w) cudaFreeHost(c->h_w);
     c->h_dst = c->h_w = nullptr;
@@ -477,7 +499,12 @@ struct ScopedTime {
     cudaStream_t s;
     cudaEvent_t a = nullptr;
     ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_, bool kernel = true) : c(c_), kind(kind_), s(s_) {
-        c->stats.kernel_launches += (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
+        const unsigned k = (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
+        if (c->capturing) {              // inside a graph body: counted per body run
+            c->loop_kernels += k;
+            return;
+        }
+        c->stats.kernel_launches += k;
         if (c->timing != 0) {
             a = pool_event(c);
             cudaEventRecord(a, s);
@@ -556,6 +583,7 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     st.hub_rep = pr ? c->d_hub_rep : nullptr;
     st.n_hub_rep = pr && c->d_hub_rep ? c->n_hub_rep : 0;
     st.prio = pr && c->priority != 0 && c->batch_mode == kBatchNone;
+    st.loop = nullptr;
     return st;
 }
 
@@ -567,8 +595,11 @@ bool second_pass_on(const hytg_ctx *c, int algo) {
 
 cudaError_t relax_any(hytg_ctx *c, const AlgoState &st, const ListArrays &la, const Summary *sum,
                       const RelaxTask &t, int cap, cudaStream_t s) {
-    if (c->batch_mode != kBatchNone)
-        return launch_relax_batched(c->bs, la, sum, t, cap, st.bm_cur, st.overflow, s);
+    if (c->batch_mode != kBatchNone) {
+        BatchState b = c->bs;
+        b.loop = st.loop;
+        return launch_relax_batched(b, la, sum, t, cap, st.bm_cur, st.overflow, s);
+    }
     return launch_relax(st, la, sum, t, cap, s);
 }
 
@@ -603,12 +634,16 @@ hytg_status ensure_batch(hytg_ctx *c, int mode) {
 // Issue planning for one iteration on s_main: counts, selection, summary
 // copy (-> ev_sum[buf]), binning (-> ev_bin), and the device-sized cache and
 // zero-copy relaxes.
+hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop);
+
+void iteration_mark(hytg_ctx *c) {
+    if (c->timing == 0) return;
+    cudaEvent_t e = pool_event(c);
+    if (cudaEventRecord(e, c->s_main) == cudaSuccess) c->iter_ev.push_back({c->iters.size(), e});
+}
+
 hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, int buf, bool with_work) {
-    if (c->timing != 0 && with_work) {
-        cudaEvent_t e = pool_event(c);
-        CK(cudaEventRecord(e, c->s_main));
-        c->iter_ev.push_back(e);
-    }
+    if (with_work) iteration_mark(c);
     GraphDev g = graph_dev(c);
     AlgoState st = algo_state(c, algo, bucket);
     PartArrays pa = part_arrays(c);
@@ -642,27 +677,130 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
     CK(cudaMemcpyAsync(c->h_sumbuf[buf], c->d_sumbuf, c->sum_host_bytes, cudaMemcpyDeviceToHost, c->s_main));
     CK(cudaEventRecord(c->ev_sum[buf], c->s_main));
     if (!with_work) return HYTG_OK;
-    { ScopedTime t(c, HYTG_K_BIN, c->s_main); CK(launch_bin(g, st, pa, la, sum, c->s_main)); }
-    CK(cudaEventRecord(c->ev_bin, c->s_main));
+    return issue_plan_tail(c, algo, bucket, c->s_main, nullptr);
+}
+
+// The device-sized part of an iteration once its routes are decided: k_bin,
+// then the cache relax (and its second pass) and the zero-copy relax.
+// `loop` is set when the launches are captured into the device loop's body:
+// they then run only if k_loop_decide gave the iteration to the device.
+hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop) {
+    GraphDev g = graph_dev(c);
+    AlgoState st = algo_state(c, algo, bucket);
+    st.loop = loop;
+    PartArrays pa = part_arrays(c);
+    ListArrays la = list_arrays(c);
+    Summary *sum = (Summary *)c->d_sumbuf;
+    { ScopedTime t(c, HYTG_K_BIN, s); CK(launch_bin(g, st, pa, la, sum, s)); }
+    if (!c->capturing) CK(cudaEventRecord(c->ev_bin, s));
     const int cap = 152 * 4;
     if (c->carve.n_cached > 0) {
         RelaxTask t{};
         t.route = kRouteCache; t.mode = kModeDevice; t.dst = c->carve.cache_dst; t.w = c->carve.cache_w;
         t.shift = 0; t.device_sized = true; t.src_len = c->carve.cache_edges;
-        ScopedTime tm(c, HYTG_K_RELAX_CACHE, c->s_main);
-        CK(relax_any(c, st, la, sum, t, cap, c->s_main));
+        ScopedTime tm(c, HYTG_K_RELAX_CACHE, s);
+        CK(relax_any(c, st, la, sum, t, cap, s));
         if (second_pass_on(c, algo))
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
                                   c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
-                                  c->d_err, c->s_main));
+                                  c->d_err, s));
     }
     {
         RelaxTask t{};
         t.route = kRouteZ; t.mode = kModeHost; t.dst = c->m_dst; t.w = c->m_w; t.shift = 0;
         t.device_sized = true; t.src_len = c->E;
-        ScopedTime tm(c, HYTG_K_RELAX_Z, c->s_main);
-        CK(relax_any(c, st, la, sum, t, cap, c->s_main));
+        ScopedTime tm(c, HYTG_K_RELAX_Z, s);
+        CK(relax_any(c, st, la, sum, t, cap, s));
     }
+    return HYTG_OK;
+}
+
+// Device loop (plain runs): whether it applies, and its graph.  The body is
+// captured once per configuration and replayed by one graph launch per
+// stretch of device iterations.
+bool loop_applies(const hytg_ctx *c) {
+    return c->device_loop != 0 && c->force_route != 5 && !c->serving;
+}
+
+hytg_status capture_loop_body(hytg_ctx *c, int algo, cudaStream_t s, unsigned long long handle) {
+    GraphDev g = graph_dev(c);
+    AlgoState st = algo_state(c, algo);
+    st.loop = c->d_loop;
+    PartArrays pa = part_arrays(c);
+    Summary *sum = (Summary *)c->d_sumbuf;
+    if (c->batch_mode != kBatchNone) {
+        // per-iteration source bookkeeping, as the host loop does it
+        BatchState b = c->bs;
+        b.loop = c->d_loop;
+        ScopedTime t(c, HYTG_K_OTHER, s);
+        CK(launch_zero_u64(c->d_alive, 1, s));
+        if (c->batch_mode == kBatchPPR)
+            CK(launch_b_take(b, c->d_off, c->n_words_alloc, c->batch_K, (float)c->pr_damping,
+                             (float)c->pr_eps, st.bm_cur, s));
+        else
+            CK(launch_b_commit(b, c->V, c->n_words_alloc, 0, st.bm_cur, s));
+    } else if (algo == kPR || algo == kPPR) {
+        ScopedTime t(c, HYTG_K_OTHER, s);
+        CK(launch_hub_reduce(st, s));
+        CK(launch_pr_frontier(st, c->V, c->n_words_alloc, s));
+    } else if (algo == kCC) {
+        ScopedTime t(c, HYTG_K_OTHER, s);
+        CK(launch_cc_jump(st, c->n_words_alloc, s));
+    }
+    {
+        const SumLayout L = sum_layout(g.N);
+        ScopedTime t(c, HYTG_K_OTHER, s);
+        CK(launch_zero_u64(pa.n_act, (L.zero_end - L.n_act) / 8, s));
+    }
+    { ScopedTime t(c, HYTG_K_COUNT, s); CK(launch_count(g, st, pa, (unsigned long long)c->m, s)); }
+    { ScopedTime t(c, HYTG_K_COUNT, s); CK(launch_select(g, pa, cost_params(c, algo, 1), sum, s)); }
+    { ScopedTime t(c, HYTG_K_OTHER, s); CK(launch_loop_decide(sum, c->d_loop, handle, s)); }
+    return issue_plan_tail(c, algo, 0xFFFFFFFFu, s, c->d_loop);
+}
+
+hytg_status ensure_loop_graph(hytg_ctx *c, int algo) {
+    char key[512];
+    std::snprintf(key, sizeof key, "%d|%d|%u|%p|%u|%llu|%d|%p|%u|%p|%p|%p|%g|%g|%g|%g|%g|%g|%g|%g|%g|%llu|%zu|%g",
+                  algo, c->batch_mode, c->batch_K, (void *)c->carve.cache_dst, c->carve.n_cached,
+                  (unsigned long long)c->carve.cache_edges, (int)second_pass_on(c, algo), (void *)c->d_hub_rep,
+                  c->n_hub_rep, (void *)c->d_sumbuf, (void *)c->d_val, (void *)c->d_ebase, c->alpha, c->beta,
+                  c->gamma, c->m, c->MR, c->force_route, c->pr_damping, c->pr_eps, c->priority,
+                  (unsigned long long)c->n_words_alloc, c->part_vb.size(), c->hub_frac);
+    if (c->loop_exec && c->loop_key == key) return HYTG_OK;
+    free_loop_graph(c);
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    c->loop_graph = g;
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(c->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->loop_kernels = 0;
+    hytg_status st = capture_loop_body(c, algo, c->s_cap, (unsigned long long)h);
+    c->capturing = false;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(c->s_cap, &captured);
+    if (st != HYTG_OK) { free_loop_graph(c); return st; }
+    if (e_end != cudaSuccess) {
+        free_loop_graph(c);
+        return fail(c, HYTG_ERR_CUDA, std::string("capture of the device loop: ") + cudaGetErrorString(e_end));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e_in = cudaGraphInstantiate(&ex, g, 0);
+    if (e_in != cudaSuccess) {
+        free_loop_graph(c);
+        return fail(c, HYTG_ERR_CUDA, std::string("instantiating the device loop: ") + cudaGetErrorString(e_in));
+    }
+    c->loop_exec = ex;
+    c->loop_key = key;
     return HYTG_OK;
 }
 
@@ -931,6 +1069,50 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     return HYTG_OK;
 }
 
+// One launch of the device loop from iteration `it`: uploads the control
+// block, replays the graph, and folds the device iterations' records and
+// totals into the run's statistics.  On return `it` and `bucket` are those
+// of the iteration the loop stopped at and `status` says why it stopped.
+hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uint64_t delta, int &status) {
+    LoopCtl &h = *c->h_loop;
+    std::memset(&h, 0, sizeof(LoopCtl));
+    h.status = kLoopRun;
+    h.it = it;
+    h.bucket = bucket;
+    h.rec_cap = c->loop_rec_cap;
+    h.delta = delta;
+    h.max_it = (unsigned long long)c->max_iters;
+    h.m = (unsigned long long)c->m;
+    h.rec = c->d_loop_rec;
+    iteration_mark(c);
+    CK(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->s_main));
+    CK(cudaGraphLaunch(c->loop_exec, c->s_main));
+    CK(cudaMemcpyAsync(c->h_loop, c->d_loop, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->s_main));
+    CK(cudaStreamSynchronize(c->s_main));
+    const uint32_t n = std::min<uint32_t>(h.n_rec, c->loop_rec_cap);
+    if (n) {
+        const size_t base = c->iters.size();
+        c->iters.resize(base + n);
+        CK(cudaMemcpy(c->iters.data() + base, c->d_loop_rec, n * sizeof(hytg_iter_record), cudaMemcpyDeviceToHost));
+    }
+    for (int r = 0; r < kRoutes; ++r) {
+        c->stats.route_partitions[r] += h.route_parts[r];
+        c->stats.route_vertices[r] += h.route_entries[r];
+        c->stats.route_edges[r] += h.route_edges[r];
+    }
+    c->stats.link_bytes[kRouteZ] += h.z_lines * (uint64_t)c->m;
+    c->stats.edges_relaxed += h.edges;
+    c->stats.vertices_processed += h.vertices;
+    c->stats.graph_launches += 1;
+    c->stats.graph_iterations += h.iterations;
+    // every body run launches the whole body; gated kernels return at once
+    c->stats.kernel_launches += (uint64_t)c->loop_kernels * ((uint64_t)(h.it - it) + 1);
+    it = h.it;
+    bucket = h.bucket;
+    status = (int)h.status;
+    return HYTG_OK;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -974,6 +1156,10 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_bsums, 64 * sizeof(double)));
     ck(cudaMalloc(&c->d_alive, sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_extra, sizeof(unsigned long long)));
+    ck(cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
+    ck(cudaMalloc(&c->d_loop, sizeof(LoopCtl)));
+    ck(cudaMalloc(&c->d_loop_rec, (size_t)c->loop_rec_cap * sizeof(hytg_iter_record)));
+    ck(cudaHostAlloc((void **)&c->h_loop, sizeof(LoopCtl), cudaHostAllocDefault));
     if (s != HYTG_OK) { hytg_destroy(c); return s; }
     *out = c;
     return HYTG_OK;
@@ -1002,6 +1188,11 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_c) cudaEventDestroy(c->ev_c);
     for (int i = 0; i < 2; ++i) if (c->ev_run[i]) cudaEventDestroy(c->ev_run[i]);
+    free_loop_graph(c);
+    dfree(c->d_loop);
+    dfree(c->d_loop_rec);
+    if (c->h_loop) cudaFreeHost(c->h_loop);
+    if (c->s_cap) cudaStreamDestroy(c->s_cap);
     delete c->pool;
     for (int i = 0; i < 2; ++i) {
         if (c->h_cstage[i]) cudaFreeHost(c->h_cstage[i]);
@@ -1194,6 +1385,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
+    else if (k == "device_loop") { if (v != 0 && v != 1) return bad(); c->device_loop = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1223,6 +1415,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "hub_replicas") *v = c->hub_replicas;
     else if (k == "compact_host") *v = c->compact_host;
     else if (k == "priority") *v = c->priority;
+    else if (k == "device_loop") *v = c->device_loop;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1298,6 +1491,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             }
         }
         uint32_t it = 0;
+        const bool use_loop = loop_applies(c);
         s = issue_plan(c, algo, bucket, it, 0, true);
         if (s != HYTG_OK) return s;
         for (;;) {
@@ -1313,7 +1507,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 bucket = (unsigned int)std::min<uint64_t>(nb, 0xFFFFFFFEull);
                 if (hs->pending_min >= 0xFFFFFFFEull) bucket = 0xFFFFFFFFu;
                 ++it;
-                s = issue_plan(c, algo, bucket, it, it & 1, true);
+                s = issue_plan(c, algo, bucket, it, it & 1, it < (uint32_t)c->max_iters);
                 if (s != HYTG_OK) return s;
                 continue;
             }
@@ -1322,7 +1516,27 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             if (s != HYTG_OK) return s;
             // --- next iteration
             ++it;
-            s = issue_plan(c, algo, bucket, it, it & 1, true);
+            if (use_loop) {
+                // iterations on the device until one needs the F or C route
+                int status = 0;
+                // captured after iteration 0 has run, so every launcher's
+                // one-time set-up happened outside the capture
+                s = ensure_loop_graph(c, algo);
+                if (s != HYTG_OK) return s;
+                s = run_device_loop(c, it, bucket, delta, status);
+                if (s != HYTG_OK) return s;
+                if (status != kLoopHost) break;       // converged or at the cap
+                const int nb = it & 1;
+                iteration_mark(c);
+                CK(cudaMemcpyAsync(c->h_sumbuf[nb], c->d_sumbuf, c->sum_host_bytes, cudaMemcpyDeviceToHost,
+                                   c->s_main));
+                CK(cudaEventRecord(c->ev_sum[nb], c->s_main));
+                s = issue_plan_tail(c, algo, bucket, c->s_main, nullptr);
+                if (s != HYTG_OK) return s;
+                continue;
+            }
+            // at the cap only the plan runs (the loop then stops on it)
+            s = issue_plan(c, algo, bucket, it, it & 1, it < (uint32_t)c->max_iters);
             if (s != HYTG_OK) return s;
         }
         c->stats.iterations = it;
@@ -1364,10 +1578,13 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats.n_sources = c->batch_K;
         c->stats.extra_edges = extra;
         c->stats.source_edges = c->batch_mode != kBatchNone ? swork : c->stats.edges_relaxed;
-        for (size_t i = 0; i + 1 < c->iter_ev.size() && i < c->iters.size(); ++i) {
+        for (size_t i = 0; i + 1 < c->iter_ev.size(); ++i) {
+            // host-issued iterations only: a mark and the next iteration's mark
+            const size_t k = c->iter_ev[i].first;
             float ms = 0;
-            if (cudaEventElapsedTime(&ms, c->iter_ev[i], c->iter_ev[i + 1]) == cudaSuccess)
-                c->iters[i].device_ms = ms;
+            if (k < c->iters.size() && c->iter_ev[i + 1].first == k + 1 &&
+                cudaEventElapsedTime(&ms, c->iter_ev[i].second, c->iter_ev[i + 1].second) == cudaSuccess)
+                c->iters[k].device_ms = ms;
         }
         for (auto &tl : c->timed) {
             float ms = 0;

@@ -87,6 +87,7 @@ __device__ __forceinline__ void next_batch(unsigned int &nz, unsigned int bits,
 
 __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArrays pa,
                                                unsigned long long m) {
+    if (st.loop) st.bucket_limit = st.loop->bucket;
     const int lane = threadIdx.x & 31;
     const unsigned long long n_rounds = g.n_words_alloc / 32;
     const bool bucketed = st.bucket_limit != 0xFFFFFFFFu;
@@ -230,10 +231,17 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
     for (int q = 0; q < 11; ++q) red[q] = 0;
     for (unsigned int p = p0; p < p1; ++p) {
         const int r = pa.route[p];
-        v[r] += pa.entries[p];
-        v[kRoutes + r] += pa.edges[p];
-        red[r] += pa.lines[p];
-        red[kRoutes + r] += 1;
+        const unsigned long long ent = pa.entries[p], edg = pa.edges[p], lin = pa.lines[p];
+        // compile-time indices keep v[] and red[] in registers
+#pragma unroll
+        for (int q = 0; q < kRoutes; ++q) {
+            if (r == q) {
+                v[q] += ent;
+                v[kRoutes + q] += edg;
+                red[q] += lin;
+                red[kRoutes + q] += 1;
+            }
+        }
         red[10] += pa.n_act[p];
     }
     unsigned long long tot[10];
@@ -253,10 +261,16 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
     }
     for (unsigned int p = p0; p < p1; ++p) {
         const int r = pa.route[p];
-        pa.route_entry[p] = v[r];
-        pa.route_edge[p] = v[kRoutes + r];
-        v[r] += pa.entries[p];
-        v[kRoutes + r] += pa.edges[p];
+        const unsigned long long ent = pa.entries[p], edg = pa.edges[p];
+#pragma unroll
+        for (int q = 0; q < kRoutes; ++q) {
+            if (r == q) {
+                pa.route_entry[p] = v[q];
+                pa.route_edge[p] = v[kRoutes + q];
+                v[q] += ent;
+                v[kRoutes + q] += edg;
+            }
+        }
     }
     if (tid == 0) {
         sum->n_active = redtot[10];
@@ -277,6 +291,10 @@ __global__ void __launch_bounds__(kSelectBlock) k_select(GraphDev g, PartArrays 
 // ---------------------------------------------------------------- k_bin
 __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArrays pa, ListArrays la,
                                              const Summary *sum) {
+    if (st.loop) {
+        if (!st.loop->work) return;
+        st.bucket_limit = st.loop->bucket;
+    }
     const int lane = threadIdx.x & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
     const unsigned long long n_rounds = g.n_words_alloc / 32;

@@ -63,6 +63,7 @@ template <int ALGO>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays la,
                                                        const Summary *sum, RelaxTask t) {
     __shared__ TileSmem<false> sm;
+    if (st.loop && !st.loop->work) return;
     const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
     const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
     if (kb >= ke) return;
@@ -176,6 +177,10 @@ __global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigne
                                                      long long shift, unsigned long long src_len,
                                                      unsigned long long vlo, unsigned long long vhi,
                                                      unsigned long long *edges_out, unsigned int *err) {
+    if (st.loop) {
+        if (!st.loop->work) return;
+        st.bucket_limit = st.loop->bucket;
+    }
     float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
     const int lane = threadIdx.x & 31;
     unsigned long long done = 0;
