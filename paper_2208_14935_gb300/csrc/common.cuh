@@ -122,6 +122,7 @@ struct GraphDev {
     unsigned long long V, n_words_alloc;
     const unsigned int *part_wb;        // partition bounds in bitmap words, N+1
     const unsigned long long *part_eb;  // partition bounds in edges, N+1
+    const unsigned int *round_part;     // partition holding word 32 * r, per 32-word round
     unsigned int N;
 };
 
@@ -204,6 +205,9 @@ struct RelaxTask {
 
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
                          const RelaxTask &t, int grid_cap, cudaStream_t s);
+// Both tasks device-sized (routes of the current list); plain runs only.
+cudaError_t launch_relax_pair(const AlgoState &st, const ListArrays &la, const Summary *sum,
+                              const RelaxTask &ta, const RelaxTask &tb, int grid, cudaStream_t s);
 cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *off,
                                const unsigned int *dst, const unsigned int *w, long long shift,
                                unsigned long long src_len, unsigned long long vlo,

@@ -169,6 +169,7 @@ struct hytg_ctx {
     std::vector<uint64_t> part_vb, part_eb;
     std::vector<uint32_t> part_wb;
     unsigned int *d_part_wb = nullptr;
+    unsigned int *d_round_part = nullptr;                // partition of each 32-word bitmap round
     unsigned long long *d_part_eb = nullptr;
 
     // vertex-side device state
@@ -285,7 +286,7 @@ void free_graph(hytg_ctx *c) {
     c->m_dst = c->m_w = nullptr;
     dfree(c->d_off); dfree(c->d_val); dfree(c->d_delta); dfree(c->d_bm[0]); dfree(c->d_bm[1]);
     dfree(c->d_out); dfree(c->d_ebase); dfree(c->d_soff); dfree(c->d_pay); dfree(c->d_tiles);
-    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm);
+    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm); dfree(c->d_round_part);
     dfree(c->d_hub_rep);
     c->n_hub_rep = 0;
     dfree(c->bs.fr); dfree(c->bs.vis); dfree(c->bs.nxt); dfree(c->bs.val);
@@ -403,7 +404,7 @@ void make_partitions(hytg_ctx *c) {
 
 hytg_status upload_partitions(hytg_ctx *c) {
     const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
-    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf);
+    dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_round_part);
     for (int i = 0; i < 2; ++i) {
         if (c->h_sumbuf[i]) cudaFreeHost(c->h_sumbuf[i]);
         c->h_sumbuf[i] = nullptr;
@@ -412,6 +413,19 @@ hytg_status upload_partitions(hytg_ctx *c) {
     CK(cudaMalloc(&c->d_part_eb, (N + 1) * sizeof(unsigned long long)));
     CK(cudaMemcpy(c->d_part_wb, c->part_wb.data(), (N + 1) * sizeof(unsigned int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_part_eb, c->part_eb.data(), (N + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    {
+        // round table for the planning kernels' partition lookup
+        const uint64_t rounds = std::max<uint64_t>(1, c->n_words_alloc / 32);
+        std::vector<uint32_t> rp(rounds);
+        uint32_t p = 0;
+        for (uint64_t r = 0; r < rounds; ++r) {
+            const uint64_t w = r * 32;
+            while (p + 1 < N && c->part_wb[p + 1] <= w) ++p;
+            rp[r] = p;
+        }
+        CK(cudaMalloc(&c->d_round_part, rounds * sizeof(uint32_t)));
+        CK(cudaMemcpy(c->d_round_part, rp.data(), rounds * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
     SumLayout L = sum_layout(N);
     c->sum_dev_bytes = L.total;
     c->sum_host_bytes = L.host_end;
@@ -526,6 +540,7 @@ GraphDev graph_dev(hytg_ctx *c) {
     g.n_words_alloc = c->n_words_alloc;
     g.part_wb = c->d_part_wb;
     g.part_eb = c->d_part_eb;
+    g.round_part = c->d_round_part;
     g.N = (unsigned int)(c->part_vb.size() - 1);
     return g;
 }
@@ -694,6 +709,23 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
     { ScopedTime t(c, HYTG_K_BIN, s); CK(launch_bin(g, st, pa, la, sum, s)); }
     if (!c->capturing) CK(cudaEventRecord(c->ev_bin, s));
     const int cap = 152 * 4;
+    if (c->capturing && c->batch_mode == kBatchNone && c->carve.n_cached > 0) {
+        // device loop body: cache and zero-copy routes in one launch
+        RelaxTask tc{}, tz{};
+        tc.route = kRouteCache; tc.mode = kModeDevice; tc.dst = c->carve.cache_dst; tc.w = c->carve.cache_w;
+        tc.shift = 0; tc.device_sized = true; tc.src_len = c->carve.cache_edges;
+        tz.route = kRouteZ; tz.mode = kModeHost; tz.dst = c->m_dst; tz.w = c->m_w; tz.shift = 0;
+        tz.device_sized = true; tz.src_len = c->E;
+        {
+            ScopedTime tm(c, HYTG_K_RELAX_Z, s);
+            CK(launch_relax_pair(st, la, sum, tc, tz, cap, s));
+        }
+        if (second_pass_on(c, algo))
+            CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
+                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
+                                  c->d_err, s));
+        return HYTG_OK;
+    }
     if (c->carve.n_cached > 0) {
         RelaxTask t{};
         t.route = kRouteCache; t.mode = kModeDevice; t.dst = c->carve.cache_dst; t.w = c->carve.cache_w;

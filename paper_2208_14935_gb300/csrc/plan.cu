@@ -23,49 +23,59 @@ namespace hytg {
 namespace {
 
 constexpr int kBatch = 4;   // bitmap words whose loads are issued together
-constexpr int kPrefetch = 8;   // bitmap rounds a warp loads before scanning them
+constexpr int kPrefetch = 8;   // 128-word blocks of the bitmap a warp loads before scanning them
 
-// This warp's rounds of 32 bitmap words (rd = warp, warp + nwarps, ...),
-// kPrefetch at a time: the words of kPrefetch rounds are loaded together so
-// their latencies overlap, and rounds whose 32 words are all zero (most of
-// them when the frontier is small) are skipped.  body(rd, bits) sees the
-// round index and this lane's word.  The walk only reads the bitmap; body
-// may rewrite its own round's words.
+// This warp's share of the bitmap, in blocks of 128 words (4 rounds of 32):
+// block b = warp, warp + nwarps, ...  Each lane loads 4 consecutive words
+// with one 16-byte load, kPrefetch blocks at a time, so their latencies
+// overlap; a round (32 words) whose words are all zero -- most of them when
+// the frontier is small -- is skipped.  body(rd, bits) sees each remaining
+// round's index and this lane's word of it (reloaded: a cache hit).  The
+// walk only reads the bitmap; body may rewrite its own round's words.
+// The bitmap is padded to a multiple of 32 words, so a block's 4-word group
+// is either wholly inside it or wholly outside.
 template <class F>
 __device__ __forceinline__ void for_rounds(const unsigned int *bm, unsigned long long n_rounds, F &&body) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    for (unsigned long long r0 = w; r0 < n_rounds; r0 += nwarps * kPrefetch) {
-        unsigned int pre[kPrefetch];
+    const unsigned long long n_words = n_rounds * 32;
+    const unsigned long long n_blocks = (n_rounds + 3) / 4;
+    const uint4 *bm4 = reinterpret_cast<const uint4 *>(bm);
+    for (unsigned long long b0 = w; b0 < n_blocks; b0 += nwarps * kPrefetch) {
+        uint4 pre[kPrefetch];
 #pragma unroll
         for (int j = 0; j < kPrefetch; ++j) {
-            const unsigned long long rd = r0 + (unsigned long long)j * nwarps;
-            pre[j] = rd < n_rounds ? bm[rd * 32 + lane] : 0u;
+            const unsigned long long blk = b0 + (unsigned long long)j * nwarps;
+            const unsigned long long word = blk * 128 + 4 * lane;
+            pre[j] = (blk < n_blocks && word < n_words) ? bm4[word / 4] : make_uint4(0u, 0u, 0u, 0u);
         }
+        // live: bit 4 j + r for round r of block j; lanes 8 r .. 8 r + 7 hold round r
         unsigned int live = 0;
 #pragma unroll
-        for (int j = 0; j < kPrefetch; ++j)
-            live |= (__any_sync(0xffffffffu, pre[j] != 0) ? 1u : 0u) << j;
+        for (int j = 0; j < kPrefetch; ++j) {
+            const unsigned int nzl = __ballot_sync(0xffffffffu, (pre[j].x | pre[j].y | pre[j].z | pre[j].w) != 0u);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if ((nzl >> (8 * r)) & 0xFFu) live |= 1u << (4 * j + r);
+        }
         while (live) {                              // warp-uniform
-            const int j = __ffs(live) - 1;
+            const int q = __ffs(live) - 1;
             live &= live - 1;
-            // reloaded (a cache hit) rather than kept live across the body
-            const unsigned long long rd = r0 + (unsigned long long)j * nwarps;
+            const unsigned long long rd = (b0 + (unsigned long long)(q >> 2) * nwarps) * 4 + (q & 3);
             body(rd, bm[rd * 32 + lane]);
         }
     }
 }
 
-// Partition holding bitmap word `widx` (bounds are word indices).
-__device__ __forceinline__ unsigned int find_part(const unsigned int *wb, unsigned int N,
-                                                  unsigned long long widx) {
-    unsigned int lo = 0, hi = N;  // invariant: wb[lo] <= widx < wb[hi]
-    while (hi - lo > 1) {
-        unsigned int mid = (lo + hi) >> 1;
-        if ((unsigned long long)__ldg(&wb[mid]) <= widx) lo = mid; else hi = mid;
-    }
-    return lo;
+// Partition holding bitmap word `widx` (bounds are word indices): the
+// partition of the word's 32-word round from the round table, then forward
+// over the partition bounds inside the round (partitions are whole words, so
+// at most 31 steps, in practice none or one).
+__device__ __forceinline__ unsigned int find_part(const GraphDev &g, unsigned long long widx) {
+    unsigned int p = __ldg(&g.round_part[widx >> 5]);
+    while (p + 1 < g.N && (unsigned long long)__ldg(&g.part_wb[p + 1]) <= widx) ++p;
+    return p;
 }
 
 // Up to kBatch nonzero words of this warp's 32-word round, in order.
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                         if (st.prio) atomicAdd(&pa.prio[cur_p], a_prio);
                     }
                     a_nact = a_ent = a_edges = a_lines = a_prio = 0;
-                    cur_p = find_part(g.part_wb, g.N, widx);
+                    cur_p = find_part(g, widx);
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
                 }
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                 if (elig == 0) continue;
                 if (lane == (int)(widx - wbase)) keep = wq[q] & ~elig;
                 if (widx < p_lo || widx >= p_hi) {
-                    cur_p = find_part(g.part_wb, g.N, widx);
+                    cur_p = find_part(g, widx);
                     p_lo = g.part_wb[cur_p];
                     p_hi = g.part_wb[cur_p + 1];
                     const int rp = pa.route[cur_p];

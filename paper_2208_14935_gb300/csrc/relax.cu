@@ -59,6 +59,40 @@ __device__ __forceinline__ void relax_edge(const AlgoState &st, unsigned int v, 
     }
 }
 
+// One tile of a relax launch: route edges [tile * kTile, ...) within [kb, ke).
+template <int ALGO>
+__device__ __forceinline__ void relax_tile(const AlgoState &st, const ListArrays &la, const Summary *sum,
+                                           const RelaxTask &t, unsigned long long tile,
+                                           unsigned long long kb, unsigned long long ke,
+                                           TileSmem<false> &sm, float *hub_rep) {
+    const bool weighted = (ALGO == kSSSP);
+    unsigned long long k0;
+    const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
+    unsigned int dv[kRelaxIPT], wv[kRelaxIPT], pv[kRelaxIPT];
+#pragma unroll
+    for (int j = 0; j < kRelaxIPT; ++j) {
+        const int slot = threadIdx.x + j * kRelaxBlock;
+        dv[j] = kInf;
+        wv[j] = 0;
+        pv[j] = 0;
+        if (slot < n) {
+            const int i = sm.sid[slot];
+            const long long e = (long long)(k0 + slot) + sm.delta[i];
+            if (e >= 0 && (unsigned long long)e < t.src_len) {
+                dv[j] = __ldg(t.dst + e);
+                if (weighted) wv[j] = __ldg(t.w + e);
+                pv[j] = sm.pay[i];
+            } else {
+                atomicOr(la.err, 8u);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kRelaxIPT; ++j)
+        if (dv[j] != kInf) relax_edge<ALGO>(st, dv[j], pv[j], wv[j], hub_rep);
+    __syncthreads();
+}
+
 template <int ALGO>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays la,
                                                        const Summary *sum, RelaxTask t) {
@@ -68,34 +102,29 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
     const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
-    const bool weighted = (ALGO == kSSSP);
     float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
-    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
-        unsigned long long k0;
-        const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
-        unsigned int dv[kRelaxIPT], wv[kRelaxIPT], pv[kRelaxIPT];
-#pragma unroll
-        for (int j = 0; j < kRelaxIPT; ++j) {
-            const int slot = threadIdx.x + j * kRelaxBlock;
-            dv[j] = kInf;
-            wv[j] = 0;
-            pv[j] = 0;
-            if (slot < n) {
-                const int i = sm.sid[slot];
-                const long long e = (long long)(k0 + slot) + sm.delta[i];
-                if (e >= 0 && (unsigned long long)e < t.src_len) {
-                    dv[j] = __ldg(t.dst + e);
-                    if (weighted) wv[j] = __ldg(t.w + e);
-                    pv[j] = sm.pay[i];
-                } else {
-                    atomicOr(la.err, 8u);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kRelaxIPT; ++j)
-            if (dv[j] != kInf) relax_edge<ALGO>(st, dv[j], pv[j], wv[j], hub_rep);
-        __syncthreads();
+    for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x)
+        relax_tile<ALGO>(st, la, sum, t, tile, kb, ke, sm, hub_rep);
+}
+
+// Two device-sized routes in one launch (cache and zero-copy in the device
+// loop, where an iteration's frontier is often a few hundred vertices and a
+// launch costs more than the work).
+template <int ALGO>
+__global__ void __launch_bounds__(kRelaxBlock) k_relax_pair(AlgoState st, ListArrays la,
+                                                            const Summary *sum, RelaxTask ta,
+                                                            RelaxTask tb) {
+    __shared__ TileSmem<false> sm;
+    if (st.loop && !st.loop->work) return;
+    float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
+    const unsigned long long ea = sum->route_edges[ta.route], eb = sum->route_edges[tb.route];
+    if (ea) {
+        for (unsigned long long tile = blockIdx.x; tile <= (ea - 1) / kTile; tile += gridDim.x)
+            relax_tile<ALGO>(st, la, sum, ta, tile, 0ull, ea, sm, hub_rep);
+    }
+    if (eb) {
+        for (unsigned long long tile = blockIdx.x; tile <= (eb - 1) / kTile; tile += gridDim.x)
+            relax_tile<ALGO>(st, la, sum, tb, tile, 0ull, eb, sm, hub_rep);
     }
 }
 
@@ -257,6 +286,17 @@ cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summar
         case kSSSP: k_relax<kSSSP><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
         case kCC: k_relax<kCC><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
         default: k_relax<kPR><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, t); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax_pair(const AlgoState &st, const ListArrays &la, const Summary *sum,
+                              const RelaxTask &ta, const RelaxTask &tb, int grid, cudaStream_t s) {
+    switch (st.algo) {
+        case kBFS: k_relax_pair<kBFS><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, ta, tb); break;
+        case kSSSP: k_relax_pair<kSSSP><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, ta, tb); break;
+        case kCC: k_relax_pair<kCC><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, ta, tb); break;
+        default: k_relax_pair<kPR><<<grid, kRelaxBlock, 0, s>>>(st, la, sum, ta, tb); break;
     }
     return cudaGetLastError();
 }
