@@ -56,6 +56,13 @@ def parse():
                     help="comma-separated subset of bfs,sssp,cc,pagerank (profiling runs)")
     ap.add_argument("--no-probe", action="store_true", help="skip the host-link probe")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain runs")
+    ap.add_argument("--mesh-only", type=int, default=0, metavar="SIDE",
+                    help="only the high-diameter workload: SIDE x SIDE 4-neighbour mesh with 0.1 %% "
+                         "local shortcuts, weights in [1, 1000], 20 %% budget; BFS, SSSP, CC from "
+                         "vertex 0 (with and without the device loop); prints its own line")
+    ap.add_argument("--autotune", action="store_true",
+                    help="with --batched-only: tune partition size, F-task width and MR on the "
+                         "batched BFS/SSSP runs first (paper_2208_14935_gb300.autotune)")
     ap.add_argument("--batched-only", type=int, default=0, metavar="SCALE",
                     help="only the batched workload (64 BFS/SSSP sources, 32 PPR seeds) on R-MAT "
                          "SCALE against the same sources run one at a time; prints its own line")
@@ -261,6 +268,17 @@ def run_batched_only(args):
     graph_bytes = g.E * 8 + (g.V + 1) * 8
     eng = hytg.Engine(g, budget=int(args.budget_frac * graph_bytes),
                       params={"part_bytes": args.part_bytes})
+    tuned = None
+    if args.autotune:
+        from paper_2208_14935_gb300.autotune import autotune
+        rng = np.random.default_rng(5)
+        cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
+        src = rng.choice(cand, 64, replace=False).tolist()
+        space = {"part_bytes": [2 << 20, 4 << 20, 8 << 20], "k": [2, 4, 8], "MR": [64, 256, 1024]}
+        t0 = time.perf_counter()
+        tuned = autotune(eng, [("bfs", src), ("sssp", src)], space=space, reps=1)
+        tuned = {"params": tuned, "seconds": round(time.perf_counter() - t0, 1),
+                 "workload": "64-source batched BFS + SSSP (other sources than the measured ones)"}
     res = batched_vs_plain(hytg, eng, g)
     eng.close()
     line = {"metric": "batched vs plain GTEPS (per-source edges relaxed / device time)",
@@ -269,7 +287,40 @@ def run_batched_only(args):
                                    f"{args.budget_frac:.0%} of graph bytes",
                        "V": g.V, "E": g.E, "budget_bytes": int(args.budget_frac * graph_bytes),
                        "graph_gen_s": round(t_gen, 1)},
-            "batched_vs_plain": res}
+            "autotuned": tuned, "batched_vs_plain": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_mesh_only(args):
+    """The road-like workload: long tails of tiny frontiers, where the
+    per-iteration cost (planning + launches) rather than the link decides."""
+    from paper_2208_14935_gb300 import build as bld
+    bld.build()
+    from paper_2208_14935_gb300 import hytg
+    from gen import graphgen as gg
+    t0 = time.perf_counter()
+    g = gg.mesh(args.mesh_only, args.mesh_only, shortcut_frac=0.001, radius=16, seed=1, wmax=1000)
+    t_gen = time.perf_counter() - t0
+    graph_bytes = g.E * 8 + (g.V + 1) * 8
+    eng = hytg.Engine(g, budget=int(0.2 * graph_bytes), params={"part_bytes": args.part_bytes})
+    res = {}
+    for loop in (1, 0):
+        eng.set_param("device_loop", loop)
+        for algo in ("bfs", "sssp", "cc"):
+            hytg.hytg_run(eng.ctx, hytg.ALGOS[algo], None if algo == "cc" else [0])
+            st = eng.stats()
+            res[f"{algo}{'' if loop else '_host_loop'}"] = {
+                "ms": round(st["device_ms"], 1), "iterations": st["iterations"],
+                "graph_iterations": st["graph_iterations"], "edges_relaxed": st["edges_relaxed"],
+                "gteps": st["edges_relaxed"] / (st["device_ms"] * 1e-3) / 1e9,
+                "us_per_iteration": round(st["device_ms"] * 1e3 / max(1, st["iterations"]), 1)}
+    eng.close()
+    line = {"metric": "mesh BFS/SSSP/CC device time (long tails of tiny frontiers)", "unit": "ms",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"mesh {args.mesh_only}x{args.mesh_only}, 0.1% shortcuts, budget 20% "
+                                   "of graph bytes", "V": g.V, "E": g.E,
+                       "budget_bytes": int(0.2 * graph_bytes), "graph_gen_s": round(t_gen, 1)},
+            "runs": res}
     print(json.dumps(line), flush=True)
 
 
@@ -279,6 +330,8 @@ def main():
         return run_reference(args)
     if args.batched_only:
         return run_batched_only(args)
+    if args.mesh_only:
+        return run_mesh_only(args)
     rank, world, local = dist_env()
     algos = [a for a in args.algos.split(",") if a]
     assert all(a in ALGOS for a in algos), args.algos
@@ -356,6 +409,8 @@ def main():
                        "kernel_ms": {hytg.KERNEL_KINDS[i]: round(kk[i], 2) for i in range(12) if kk[i]},
                        "iterations": st["iterations"], "edges_relaxed": st["edges_relaxed"],
                        "second_pass_edges": st["extra_edges"],
+                       "second_pass_ms": round(sum(p[a]["stats"]["second_pass_ms"] for p in steps) / len(steps), 2),
+                       "graph_iterations": st["graph_iterations"],
                        "route_partitions": dict(zip(hytg.ROUTE_NAMES, st["route_partitions"])),
                        "route_edges": dict(zip(hytg.ROUTE_NAMES, st["route_edges"])),
                        "link_bytes": sum(st["link_bytes"])}

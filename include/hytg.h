@@ -100,6 +100,8 @@ typedef struct hytg_stats {
                                          host threads ("compact_host" > 0), else 0 */
     uint64_t graph_launches;          /* launches of the device-loop graph ("device_loop") */
     uint64_t graph_iterations;        /* iterations run entirely inside those launches */
+    double second_pass_ms;            /* device time of the second passes (timing on) */
+    uint64_t second_pass_count;       /* second-pass launches timed */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */

@@ -38,6 +38,7 @@ using namespace hytg;
 namespace {
 
 constexpr int kMaxStreams = 8;
+constexpr int kKindSecondPass = 12;     // timed kind beyond HYTG_K_*: hytg_stats.second_pass_ms
 
 struct TimedLaunch {
     int kind;
@@ -608,6 +609,13 @@ bool second_pass_on(const hytg_ctx *c, int algo) {
     return c->two_pass == 2 || algo == kPR || algo == kPPR;
 }
 
+// The cache range gets its second pass only when every cached partition is
+// routed to the cache (always, under the cost model); a forced route could
+// send a cached partition to F, whose own second pass would then overlap.
+bool cache_second_pass_on(const hytg_ctx *c, int algo) {
+    return second_pass_on(c, algo) && (c->force_route == -1 || c->force_route == 1);
+}
+
 cudaError_t relax_any(hytg_ctx *c, const AlgoState &st, const ListArrays &la, const Summary *sum,
                       const RelaxTask &t, int cap, cudaStream_t s) {
     if (c->batch_mode != kBatchNone) {
@@ -720,22 +728,28 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
             ScopedTime tm(c, HYTG_K_RELAX_Z, s);
             CK(launch_relax_pair(st, la, sum, tc, tz, cap, s));
         }
-        if (second_pass_on(c, algo))
+        if (cache_second_pass_on(c, algo)) {
+            ScopedTime tm(c, kKindSecondPass, s);
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
                                   c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
                                   c->d_err, s));
+        }
         return HYTG_OK;
     }
     if (c->carve.n_cached > 0) {
         RelaxTask t{};
         t.route = kRouteCache; t.mode = kModeDevice; t.dst = c->carve.cache_dst; t.w = c->carve.cache_w;
         t.shift = 0; t.device_sized = true; t.src_len = c->carve.cache_edges;
-        ScopedTime tm(c, HYTG_K_RELAX_CACHE, s);
-        CK(relax_any(c, st, la, sum, t, cap, s));
-        if (second_pass_on(c, algo))
+        {
+            ScopedTime tm(c, HYTG_K_RELAX_CACHE, s);
+            CK(relax_any(c, st, la, sum, t, cap, s));
+        }
+        if (cache_second_pass_on(c, algo)) {
+            ScopedTime tm(c, kKindSecondPass, s);
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
                                   c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
                                   c->d_err, s));
+        }
     }
     {
         RelaxTask t{};
@@ -1031,9 +1045,11 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         {
             ScopedTime tm(c, HYTG_K_RELAX_F, fs);
             CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
-            if (second_pass_on(c, algo))
-                CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
-                                      edges, c->part_vb[i0], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
+        }
+        if (second_pass_on(c, algo)) {
+            ScopedTime tm(c, kKindSecondPass, fs);
+            CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
+                                  edges, c->part_vb[i0], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
         }
         f_bytes += edges * ebytes;
         ++n_tasks;
@@ -1621,8 +1637,13 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         for (auto &tl : c->timed) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, tl.a, tl.b) == cudaSuccess) {
-                c->stats.kernel_ms[tl.kind] += ms;
-                c->stats.kernel_count[tl.kind] += 1;
+                if (tl.kind == kKindSecondPass) {
+                    c->stats.second_pass_ms += ms;
+                    c->stats.second_pass_count += 1;
+                } else {
+                    c->stats.kernel_ms[tl.kind] += ms;
+                    c->stats.kernel_count[tl.kind] += 1;
+                }
             }
         }
         cudaGetLastError();

@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Sum
 // during this iteration (PageRank: delta > eps; others: frontier bit set and,
 // for bucketed SSSP, dist below the bucket) are taken and pushed along their
 // edges in `dst`/`w`, which hold CSR edges [shift, shift + src_len).
-// A lane owns a vertex of up to 32 edges; a warp shares the edges of a vertex
-// with up to kSecondPassMaxDeg; larger vertices stay active for the next
+// A warp takes 32 consecutive vertices; vertices with more than
+// kSecondPassMaxDeg edges are not taken and stay active for the next
 // iteration's load-balanced relax.
 constexpr unsigned long long kSecondPassMaxDeg = 4096;
 
@@ -181,10 +181,13 @@ template <int ALGO>
 __device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned long long v,
                                                  unsigned long long deg, unsigned int &pay) {
     if (ALGO == kPR || ALGO == kPPR) {
-        if (__ldcg(&st.delta[v]) <= st.eps) return false;
-        const float dl = atomicExch(&st.delta[v], 0.0f);
-        // atomic: with a forced route, an F range can overlap the cache range,
-        // and the two second passes may each take a share of v's delta
+        // Take the delta seen now and subtract it with a reduction, so that
+        // pushes landing on v meanwhile (relaxes of other streams) stay in
+        // delta for later; no second pass overlaps this vertex range, so
+        // nothing else takes v concurrently.
+        const float dl = __ldcg(&st.delta[v]);
+        if (dl <= st.eps) return false;
+        atomicAdd(&st.delta[v], -dl);
         atomicAdd(&st.rank[v], dl);
         if (deg == 0) return false;
         pay = __float_as_uint(st.damping * dl / (float)deg);
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigne
     const unsigned long long first = vlo + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull);
     for (unsigned long long base = first; base < vhi; base += stride) {
         const unsigned long long v = base + lane;
-        unsigned long long e0 = 0, deg = 0;
+        unsigned long long e0 = ~0ull, deg = 0;       // lanes past vhi own no edge
         unsigned int pay = 0;
         bool mine = false;
         if (v < vhi) {
@@ -225,29 +228,67 @@ __global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigne
             deg = off[v + 1] - e0;
             if (deg <= kSecondPassMaxDeg) mine = second_pass_take<ALGO>(st, v, deg, pay);
         }
-        // lane-owned small lists
-        if (mine && deg <= 32) {
-            for (unsigned long long k = 0; k < deg; ++k) {
-                const long long i = (long long)(e0 + k) - shift;
-                if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
-                relax_edge<ALGO>(st, __ldg(dst + i), pay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
+        const unsigned int mask = __ballot_sync(0xffffffffu, mine);
+        if (mask == 0) continue;                       // warp-uniform
+        const unsigned long long act = warp_sum_u64(mine ? deg : 0ull);
+        if (lane == 0) done += act;
+        // The 32 vertices are consecutive, so their lists form one CSR range
+        // [E0, E1).  If at least half of it belongs to taken vertices, the
+        // warp streams the range with coalesced loads and each lane finds the
+        // owner of its edge among the 32 list starts; otherwise it walks the
+        // taken vertices one at a time.
+        const int last = (int)((vhi - 1 - base) < 31 ? (vhi - 1 - base) : 31);
+        const unsigned long long E0 = __shfl_sync(0xffffffffu, e0, 0);
+        const unsigned long long E1 = __shfl_sync(0xffffffffu, e0 + deg, last);
+        if (2 * act >= E1 - E0) {
+            // kStream chunks of 32 edges per round: owners and loads of all
+            // chunks first, then the pushes, so the loads overlap
+            constexpr int kStream = 4;
+            for (unsigned long long c0 = E0; c0 < E1; c0 += 32 * kStream) {
+                unsigned int dv[kStream], wv[kStream], pv[kStream];
+                bool ok[kStream];
+#pragma unroll
+                for (int q = 0; q < kStream; ++q) {
+                    const unsigned long long k = c0 + 32 * q + lane;
+                    int own = 0;                       // largest lane whose list starts at or before k
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const unsigned long long cand = __shfl_sync(0xffffffffu, e0, own + step);
+                        if (cand <= k) own += step;
+                    }
+                    pv[q] = __shfl_sync(0xffffffffu, pay, own);
+                    ok[q] = k < E1 && ((mask >> own) & 1u);
+                    dv[q] = 0;
+                    wv[q] = 0;
+                    if (ok[q]) {
+                        const long long i = (long long)k - shift;
+                        if (i < 0 || (unsigned long long)i >= src_len) {
+                            atomicOr(err, 16u);
+                            ok[q] = false;
+                        } else {
+                            dv[q] = __ldg(dst + i);
+                            if (ALGO == kSSSP) wv[q] = __ldg(w + i);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kStream; ++q)
+                    if (ok[q]) relax_edge<ALGO>(st, dv[q], pv[q], wv[q], hub_rep);
             }
-            done += deg;
-        }
-        // warp-shared medium lists
-        unsigned int coop = __ballot_sync(0xffffffffu, mine && deg > 32);
-        while (coop) {
-            const int src = __ffs(coop) - 1;
-            coop &= coop - 1;
-            const unsigned long long ce0 = __shfl_sync(0xffffffffu, e0, src);
-            const unsigned long long cdeg = __shfl_sync(0xffffffffu, deg, src);
-            const unsigned int cpay = __shfl_sync(0xffffffffu, pay, src);
-            for (unsigned long long k = lane; k < cdeg; k += 32) {
-                const long long i = (long long)(ce0 + k) - shift;
-                if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
-                relax_edge<ALGO>(st, __ldg(dst + i), cpay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
+        } else {
+            unsigned int m = mask;
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned long long ce0 = __shfl_sync(0xffffffffu, e0, src);
+                const unsigned long long cdeg = __shfl_sync(0xffffffffu, deg, src);
+                const unsigned int cpay = __shfl_sync(0xffffffffu, pay, src);
+                for (unsigned long long k = lane; k < cdeg; k += 32) {
+                    const long long i = (long long)(ce0 + k) - shift;
+                    if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
+                    relax_edge<ALGO>(st, __ldg(dst + i), cpay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
+                }
             }
-            if (lane == 0) done += cdeg;
         }
     }
     done = warp_sum_u64(done);

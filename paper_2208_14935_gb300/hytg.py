@@ -39,7 +39,8 @@ class hytg_stats(ctypes.Structure):
                 ("wall_ms", dbl), ("kernel_ms", dbl * 12), ("kernel_count", u64 * 12),
                 ("pr_residual_sum", dbl), ("pr_rank_sum", dbl), ("device_ms", dbl),
                 ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64),
-                ("host_compact_ms", dbl), ("graph_launches", u64), ("graph_iterations", u64)]
+                ("host_compact_ms", dbl), ("graph_launches", u64), ("graph_iterations", u64),
+                ("second_pass_ms", dbl), ("second_pass_count", u64)]
 
 
 class hytg_info(ctypes.Structure):
