@@ -102,6 +102,7 @@ typedef struct hytg_stats {
     uint64_t graph_iterations;        /* iterations run entirely inside those launches */
     double second_pass_ms;            /* device time of the second passes (timing on) */
     uint64_t second_pass_count;       /* second-pass launches timed */
+    uint64_t second_pass_vertices;    /* vertices scanned by host-issued second passes */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */

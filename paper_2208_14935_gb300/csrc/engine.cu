@@ -749,6 +749,7 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
                                   c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
                                   c->d_err, s));
+            c->stats.second_pass_vertices += c->part_vb[c->carve.n_cached];
         }
     }
     {
@@ -1050,6 +1051,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             ScopedTime tm(c, kKindSecondPass, fs);
             CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
                                   edges, c->part_vb[i0], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
+            c->stats.second_pass_vertices += c->part_vb[j + 1] - c->part_vb[i0];
         }
         f_bytes += edges * ebytes;
         ++n_tasks;
