@@ -321,11 +321,9 @@ void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &
     for (auto &x : th) x.join();
 }
 
-// Layout of the summary buffer: Summary, then per-partition arrays; the
-// prefix up to `route` is copied to the host each iteration.
 // Layout of the summary buffer: the Summary, then the per-partition arrays.
-// [n_act, pend_inv] is zeroed before every count; the whole buffer is copied
-// to the host once per iteration.
+// [n_act, zero_end) is zeroed before every count; [0, host_end) is copied to
+// the host once per iteration.
 struct SumLayout {
     size_t n_act, entries, edges, lines, cursor, prio, pending, pend_inv, zero_end, route_entry,
         route_edge, route, host_end, total;
