@@ -49,3 +49,33 @@ def test_binding_fails_loudly_without_library(tmp_path):
             hytg.load(str(tmp_path / "missing.so"))
     finally:
         hytg._lib = saved
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the C compiler's size and
+    field offsets (a drift would silently misread statistics)."""
+    import subprocess
+    from paper_2208_14935_gb300 import hytg
+    structs = {"hytg_stats": hytg.hytg_stats, "hytg_info": hytg.hytg_info,
+               "hytg_iter_record": hytg.hytg_iter_record, "hytg_cost_params": hytg.hytg_cost_params}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hytg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
