@@ -398,6 +398,14 @@ def main():
     # host link: bytes moved over the link by the F, C and Z routes / device time
     link_bytes = sum(sum(p[a]["stats"]["link_bytes"]) for p in steps for a in algos)
     link_gbs = link_bytes / (dev_ms * 1e-3) / 1e9
+    # per route: its bytes over the time its transfers were in flight (union
+    # over streams of the F copies / C gathers / Z relaxes, timing on)
+    per_route = {}
+    for r, name in ((2, "F"), (3, "C"), (4, "Z")):
+        b = sum(p[a]["stats"]["link_bytes"][r] for p in steps for a in algos)
+        busy = sum(p[a]["stats"]["route_busy_ms"][r] for p in steps for a in algos)
+        per_route[name] = {"bytes": b, "busy_ms": round(busy, 2),
+                           "gbs": b / (busy * 1e-3) / 1e9 if busy > 0 else None}
     per_algo = {}
     for a in algos:
         ed = sum(p[a]["stats"]["edges_relaxed"] + p[a]["stats"]["extra_edges"] for p in steps)
@@ -522,7 +530,10 @@ def main():
                    "graph_gen_s": round(t_gen, 1)},
         "host_link": {"achieved_gbs": link_gbs, "memcpy_probe_gbs": memcpy_gbs,
                       "zerocopy_probe_gbs": zc_gbs, "frac_of_measured": link_gbs / memcpy_gbs,
-                      "bytes_per_step": link_per_step},
+                      "bytes_per_step": link_per_step,
+                      "while_transferring": {k: dict(v, frac_of_measured=(v["gbs"] / memcpy_gbs
+                                                                         if v["gbs"] else None))
+                                             for k, v in per_route.items()}},
         "batched_vs_plain": batched,
         "roofline": roofline,
         "roofline_l2": roofline_l2,

@@ -77,13 +77,17 @@ typedef struct hytg_stats {
     uint64_t route_vertices[5];       /* active vertices (degree > 0) per route */
     uint64_t route_edges[5];          /* active edges per route */
     uint64_t link_bytes[5];           /* host-link bytes per route: F whole partitions,
-                                         C and Z 128-byte lines spanned, cache 0 */
+                                         C and Z 128-byte lines spanned (C with
+                                         "compact_host": the active edge bytes plus 16 B of
+                                         list index per vertex), cache 0 */
     uint64_t cache_fill_bytes;        /* bytes copied to fill the resident cache this run */
     uint64_t f_tasks;                 /* F copy tasks after combination (Sec. V-B) */
     uint64_t kernel_launches;         /* kernels launched by the run */
     double wall_ms;                   /* host wall time of hytg_run */
     double kernel_ms[12];             /* device time per kernel kind (CUDA events), when
-                                         the "timing" parameter is 1; see HYTG_K_* */
+                                         the "timing" parameter is 1; see HYTG_K_*.
+                                         Host-issued launches only: iterations run in the
+                                         device loop are not split by kind */
     uint64_t kernel_count[12];        /* launches per kernel kind (timing on) */
     double pr_residual_sum;           /* PageRank/PPR: sum of |delta| left at convergence */
     double pr_rank_sum;               /* PageRank/PPR: sum of raw ranks */
@@ -103,6 +107,11 @@ typedef struct hytg_stats {
     double second_pass_ms;            /* device time of the second passes (timing on) */
     uint64_t second_pass_count;       /* second-pass launches timed */
     uint64_t second_pass_vertices;    /* vertices scanned by host-issued second passes */
+    double route_busy_ms[5];          /* timing on: wall time during which the route's
+                                         transfers were in flight (union over streams of the
+                                         F copies, the C gathers, the Z relaxes); with
+                                         link_bytes it gives the link rate while a route
+                                         transfers.  Index: hytg_route */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */

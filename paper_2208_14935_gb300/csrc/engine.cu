@@ -1634,6 +1634,36 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 cudaEventElapsedTime(&ms, c->iter_ev[i].second, c->iter_ev[i + 1].second) == cudaSuccess)
                 c->iters[k].device_ms = ms;
         }
+        {
+            // busy time of each route's transfers: union of their intervals
+            // (relative to the run's start event) over all streams
+            std::vector<std::pair<float, float>> iv[kRoutes];
+            for (auto &tl : c->timed) {
+                const int r = tl.kind == HYTG_K_COPY_F ? kRouteF
+                            : tl.kind == HYTG_K_GATHER_C ? kRouteC
+                            : tl.kind == HYTG_K_RELAX_Z ? kRouteZ : -1;
+                float t0 = 0, t1 = 0;
+                if (r < 0 || cudaEventElapsedTime(&t0, c->ev_run[0], tl.a) != cudaSuccess ||
+                    cudaEventElapsedTime(&t1, c->ev_run[0], tl.b) != cudaSuccess)
+                    continue;
+                iv[r].push_back({t0, t1});
+            }
+            for (int r = 0; r < kRoutes; ++r) {
+                std::sort(iv[r].begin(), iv[r].end());
+                double busy = 0, lo = 0, hi = -1;
+                for (auto &p : iv[r]) {
+                    if (p.first > hi) {
+                        if (hi > lo) busy += hi - lo;
+                        lo = p.first;
+                        hi = p.second;
+                    } else if (p.second > hi) {
+                        hi = p.second;
+                    }
+                }
+                if (hi > lo) busy += hi - lo;
+                c->stats.route_busy_ms[r] = busy;
+            }
+        }
         for (auto &tl : c->timed) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, tl.a, tl.b) == cudaSuccess) {

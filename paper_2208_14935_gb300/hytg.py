@@ -40,7 +40,8 @@ class hytg_stats(ctypes.Structure):
                 ("pr_residual_sum", dbl), ("pr_rank_sum", dbl), ("device_ms", dbl),
                 ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64),
                 ("host_compact_ms", dbl), ("graph_launches", u64), ("graph_iterations", u64),
-                ("second_pass_ms", dbl), ("second_pass_count", u64), ("second_pass_vertices", u64)]
+                ("second_pass_ms", dbl), ("second_pass_count", u64), ("second_pass_vertices", u64),
+                ("route_busy_ms", dbl * 5)]
 
 
 class hytg_info(ctypes.Structure):
