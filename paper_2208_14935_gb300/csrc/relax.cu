@@ -183,12 +183,13 @@ __device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned l
     if (ALGO == kPR || ALGO == kPPR) {
         // Take the delta seen now and subtract it with a reduction, so that
         // pushes landing on v meanwhile (relaxes of other streams) stay in
-        // delta for later; no second pass overlaps this vertex range, so
-        // nothing else takes v concurrently.
+        // delta for later.  No second pass overlaps this vertex range and
+        // k_bin never runs beside one, so this thread is the only writer of
+        // rank[v] now: a plain update suffices.
         const float dl = __ldcg(&st.delta[v]);
         if (dl <= st.eps) return false;
         atomicAdd(&st.delta[v], -dl);
-        atomicAdd(&st.rank[v], dl);
+        st.rank[v] += dl;
         if (deg == 0) return false;
         pay = __float_as_uint(st.damping * dl / (float)deg);
         return true;
