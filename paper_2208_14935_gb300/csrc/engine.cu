@@ -403,6 +403,7 @@ void make_partitions(hytg_ctx *c) {
 
 hytg_status upload_partitions(hytg_ctx *c) {
     const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    free_loop_graph(c);             // its body holds the arrays freed here
     dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_round_part);
     for (int i = 0; i < 2; ++i) {
         if (c->h_sumbuf[i]) cudaFreeHost(c->h_sumbuf[i]);
