@@ -541,6 +541,9 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d + link_per_step,
                 "d2h_bytes_per_step": d2h},
+        # Graph500-style BFS rate: each reached vertex's out-edges are relaxed
+        # exactly once, so the BFS edge count is |E_reached|
+        "graph500_bfs_gteps": (per_algo["bfs"]["gteps"] if "bfs" in per_algo else None),
         "gpu_launches": launches,
         "clocks": clk,
         "per_algo": per_algo,
