@@ -223,11 +223,23 @@ def cpu_oracle_sample(g, budget_s: float = 20.0):
     return edges, secs, sample
 
 
+def step_config(args, g, s, algos, world):
+    """The bench step's `config`, shared by both arms."""
+    graph_bytes = g.E * 8 + (g.V + 1) * 8
+    sym_bytes = s.E * 4 + (s.V + 1) * 8
+    return {"workload": f"rmat{args.scale} {'+'.join(algos)}, edges in pinned host memory, "
+                        f"budget {args.budget_frac:.0%} of graph bytes",
+            "V": g.V, "E": g.E, "E_sym": s.E, "budget_bytes": int(args.budget_frac * graph_bytes),
+            "budget_bytes_cc": int(args.budget_frac * sym_bytes),
+            "part_bytes": args.part_bytes, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (edge arrays in host memory)"}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    g, _ = make_graphs(args.scale)
+    g, s = make_graphs(args.scale)
     from oracle import oracle as orc
     orc.build()
     total_e, total_s = 0, 0.0
@@ -245,7 +257,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"rmat{args.scale} BFS (oracle, CPU, 1 thread)"},
+            "config": step_config(args, g, s, [a for a in args.algos.split(",") if a], 1),
             "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -521,13 +533,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 (PageRank f32)", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale} {'+'.join(algos)}, edges in pinned host memory, "
-                               f"budget {args.budget_frac:.0%} of graph bytes",
-                   "V": g.V, "E": g.E, "E_sym": s.E, "budget_bytes": int(args.budget_frac * graph_bytes),
-                   "budget_bytes_cc": int(args.budget_frac * sym_bytes),
-                   "part_bytes": args.part_bytes, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (edge arrays in host memory, 2 GiB + 2 GiB)",
-                   "graph_gen_s": round(t_gen, 1)},
+        "config": dict(step_config(args, g, s, algos, world), graph_gen_s=round(t_gen, 1)),
         "host_link": {"achieved_gbs": link_gbs, "memcpy_probe_gbs": memcpy_gbs,
                       "zerocopy_probe_gbs": zc_gbs, "frac_of_measured": link_gbs / memcpy_gbs,
                       "bytes_per_step": link_per_step,
