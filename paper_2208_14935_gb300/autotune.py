@@ -45,12 +45,14 @@ def autotune(eng: "hytg.Engine", workload: Sequence[tuple], space: Optional[Dict
         return sum(_measure(eng, algo, src, reps) for algo, src in workload)
 
     best_cost = cost()
+    seen = {tuple(sorted(best.items())): best_cost}   # settings already measured
     if log:
         log(f"start {best} -> {best_cost:.2f} ms")
     for _ in range(rounds):
         for key, values in space.items():
             for v in values:
-                if v == best[key]:
+                trial = tuple(sorted(dict(best, **{key: v}).items()))
+                if v == best[key] or trial in seen:
                     continue
                 try:
                     eng.set_param(key, v)
@@ -58,6 +60,7 @@ def autotune(eng: "hytg.Engine", workload: Sequence[tuple], space: Optional[Dict
                 except hytg.HytgError:
                     eng.set_param(key, best[key])
                     continue
+                seen[trial] = c
                 if log:
                     log(f"  {key}={v} -> {c:.2f} ms")
                 if c < best_cost:
