@@ -245,6 +245,8 @@ struct hytg_ctx {
     uint32_t loop_rec_cap = 4096;
     uint32_t loop_kernels = 0;                           // kernels in one body iteration
     bool capturing = false;
+    bool loop_unavailable = false;                       // the graph could not be built here
+    std::string loop_error;
 };
 
 namespace {
@@ -1565,13 +1567,19 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             if (s != HYTG_OK) return s;
             // --- next iteration
             ++it;
-            if (use_loop) {
+            if (use_loop && !c->loop_unavailable) {
+                // captured after iteration 0 has run, so every launcher's
+                // one-time set-up happened outside the capture; a driver that
+                // cannot build the graph leaves this context on the host loop
+                if (ensure_loop_graph(c, algo) != HYTG_OK) {
+                    c->loop_unavailable = true;
+                    c->loop_error = c->err;
+                    cudaGetLastError();
+                }
+            }
+            if (use_loop && !c->loop_unavailable) {
                 // iterations on the device until one needs the F or C route
                 int status = 0;
-                // captured after iteration 0 has run, so every launcher's
-                // one-time set-up happened outside the capture
-                s = ensure_loop_graph(c, algo);
-                if (s != HYTG_OK) return s;
                 s = run_device_loop(c, it, bucket, delta, status);
                 if (s != HYTG_OK) return s;
                 if (status != kLoopHost) break;       // converged or at the cap
