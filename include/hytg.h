@@ -112,6 +112,9 @@ typedef struct hytg_stats {
                                          F copies, the C gathers, the Z relaxes); with
                                          link_bytes it gives the link rate while a route
                                          transfers.  Index: hytg_route */
+    double kernel_busy_ms[13];        /* timing on: union over streams of the launches of
+                                         each HYTG_K_* kind (index 12: the second pass), i.e.
+                                         the wall time during which that kind was running */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */

@@ -1644,23 +1644,24 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 c->iters[k].device_ms = ms;
         }
         {
-            // busy time of each route's transfers: union of their intervals
-            // (relative to the run's start event) over all streams
-            std::vector<std::pair<float, float>> iv[kRoutes];
+            // busy time of each kernel kind and of each route's transfers:
+            // the union of their intervals (relative to the run's start
+            // event) over all streams
+            constexpr int kKinds = kKindSecondPass + 1;
+            std::vector<std::pair<float, float>> iv[kKinds];
             for (auto &tl : c->timed) {
-                const int r = tl.kind == HYTG_K_COPY_F ? kRouteF
-                            : tl.kind == HYTG_K_GATHER_C ? kRouteC
-                            : tl.kind == HYTG_K_RELAX_Z ? kRouteZ : -1;
                 float t0 = 0, t1 = 0;
-                if (r < 0 || cudaEventElapsedTime(&t0, c->ev_run[0], tl.a) != cudaSuccess ||
+                if (tl.kind < 0 || tl.kind >= kKinds ||
+                    cudaEventElapsedTime(&t0, c->ev_run[0], tl.a) != cudaSuccess ||
                     cudaEventElapsedTime(&t1, c->ev_run[0], tl.b) != cudaSuccess)
                     continue;
-                iv[r].push_back({t0, t1});
+                iv[tl.kind].push_back({t0, t1});
             }
-            for (int r = 0; r < kRoutes; ++r) {
-                std::sort(iv[r].begin(), iv[r].end());
+            double busy_of[kKinds] = {};
+            for (int k = 0; k < kKinds; ++k) {
+                std::sort(iv[k].begin(), iv[k].end());
                 double busy = 0, lo = 0, hi = -1;
-                for (auto &p : iv[r]) {
+                for (auto &p : iv[k]) {
                     if (p.first > hi) {
                         if (hi > lo) busy += hi - lo;
                         lo = p.first;
@@ -1670,8 +1671,12 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                     }
                 }
                 if (hi > lo) busy += hi - lo;
-                c->stats.route_busy_ms[r] = busy;
+                busy_of[k] = busy;
+                c->stats.kernel_busy_ms[k] = busy;
             }
+            c->stats.route_busy_ms[kRouteF] = busy_of[HYTG_K_COPY_F];
+            c->stats.route_busy_ms[kRouteC] = busy_of[HYTG_K_GATHER_C];
+            c->stats.route_busy_ms[kRouteZ] = busy_of[HYTG_K_RELAX_Z];
         }
         for (auto &tl : c->timed) {
             float ms = 0;

@@ -41,7 +41,7 @@ class hytg_stats(ctypes.Structure):
                 ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64),
                 ("host_compact_ms", dbl), ("graph_launches", u64), ("graph_iterations", u64),
                 ("second_pass_ms", dbl), ("second_pass_count", u64), ("second_pass_vertices", u64),
-                ("route_busy_ms", dbl * 5)]
+                ("route_busy_ms", dbl * 5), ("kernel_busy_ms", dbl * 13)]
 
 
 class hytg_info(ctypes.Structure):
