@@ -193,8 +193,8 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * iteration needs the F or C route, whose copies the host issues, or the
  * run ends; 0: the host drives every iteration.  Iterations run in the
  * graph report no per-iteration device time and are not in kernel_ms; if
- * the graph cannot be built on this driver, the context keeps using the
- * host loop and graph_launches stays 0).
+ * the installed CUDA driver cannot build the graph, the context keeps using
+ * the host loop and graph_launches stays 0).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);

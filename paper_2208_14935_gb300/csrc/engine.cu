@@ -1569,7 +1569,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             ++it;
             if (use_loop && !c->loop_unavailable) {
                 // captured after iteration 0 has run, so every launcher's
-                // one-time set-up happened outside the capture; a driver that
+                // one-time set-up happened outside the capture; a CUDA driver that
                 // cannot build the graph leaves this context on the host loop
                 if (ensure_loop_graph(c, algo) != HYTG_OK) {
                     c->loop_unavailable = true;
