@@ -3,8 +3,8 @@
 //             128-byte lines (footnote to Eq. 3);
 //   k_select  one block: the engine of every partition from Eq. 1-3 and the
 //             selection rule, then the prefix sums that give each partition
-//             its place in its route's list ("pre-combine on GPU", Alg. 1
-//             lines for Vc and Vz);
+//             its place in its route's list (Alg. 1 gathers the C and the Z
+//             partitions into one batch each on the GPU);
 //   k_bin     writes the route lists (edge base, row offset, pushed value)
 //             and the tile index of the load-balanced relax kernels, takes the
 //             delta of delta-PageRank, and clears the bits it consumed.
