@@ -1,4 +1,4 @@
-"""Host logic of the serving loop (no GPU): the Poisson request generator."""
+"""Host logic of the serving loop (no GPU): the Poisson request generator, the latency statistics and the continuous-batching loop against a fake of the serving calls."""
 import numpy as np
 
 from paper_2208_14935_gb300.serve import poisson_requests, Request, latency_stats
@@ -24,3 +24,75 @@ def test_latency_stats():
     done = [Request(i, 0.0, "bfs", 0, 0.0, 0.001 * (i + 1)) for i in range(100)]
     st = latency_stats(done)
     assert st["n"] == 100 and abs(st["p50_ms"] - 50.5) < 1e-6 and st["p99_ms"] > 99
+
+
+class _FakeServeLib:
+    """Stands in for the serving calls of the C ABI: a query admitted with
+    source s converges after (s % 5) + 1 steps of its engine; the result is
+    the source repeated (so each retired query can be checked)."""
+
+    def __init__(self):
+        self.ctx = {}
+
+    def begin(self, ctx, algo, slots):
+        self.ctx[ctx] = {"slots": slots, "busy": {}, "steps": 0, "open": True}
+
+    def admit(self, ctx, slot, source):
+        c = self.ctx[ctx]
+        assert c["open"] and slot not in c["busy"] and 0 <= slot < c["slots"]
+        c["busy"][slot] = [source, (source % 5) + 1]
+
+    def step(self, ctx):
+        c = self.ctx[ctx]
+        c["steps"] += 1
+        fin = 0
+        for slot, q in c["busy"].items():
+            q[1] -= 1
+            if q[1] == 0:
+                fin |= 1 << slot
+        busy = sum(1 << s for s in c["busy"])
+        return fin, busy
+
+    def fetch(self, ctx, slot, V, algo):
+        src, left = self.ctx[ctx]["busy"].pop(slot)
+        assert left == 0
+        return np.full(V, src, np.uint32)
+
+    def end(self, ctx):
+        self.ctx[ctx]["open"] = False
+
+
+def test_continuous_batching_loop(monkeypatch):
+    from paper_2208_14935_gb300 import hytg
+    from paper_2208_14935_gb300.serve import Server
+
+    lib = _FakeServeLib()
+    monkeypatch.setattr(hytg, "hytg_serve_begin", lib.begin)
+    monkeypatch.setattr(hytg, "hytg_serve_admit", lib.admit)
+    monkeypatch.setattr(hytg, "hytg_serve_step", lib.step)
+    monkeypatch.setattr(hytg, "hytg_serve_fetch", lib.fetch)
+    monkeypatch.setattr(hytg, "hytg_serve_end", lib.end)
+
+    class Eng:
+        def __init__(self, name):
+            self.ctx = name
+            self.V = 8
+
+    engines = {"bfs": Eng("b"), "sssp": Eng("s"), "ppr": Eng("p")}
+    srv = Server(engines, slots={"bfs": 3, "sssp": 2, "ppr": 1})
+    pools = {"bfs": np.arange(0, 40), "sssp": np.arange(40, 80), "ppr": np.arange(80, 120)}
+    reqs = poisson_requests(60, float("inf"), pools, seed=2)     # all at t = 0: slots bound admission
+    done = srv.run(reqs)
+    assert sorted(r.rid for r in done) == list(range(60))         # every query retired once
+    for r in done:
+        assert np.all(r.result == r.source)                        # its own slot's result
+        assert r.arrival <= r.admitted <= r.done
+    assert all(not c["open"] and not c["busy"] for c in lib.ctx.values())
+    # each engine stepped only while it had work, and never more than its
+    # queries' total steps (batching shares steps between queries)
+    for name, algo in (("b", "bfs"), ("s", "sssp"), ("p", "ppr")):
+        total = sum((r.source % 5) + 1 for r in reqs if r.algo == algo)
+        assert 0 < lib.ctx[name]["steps"] <= total
+    # the single-slot engine runs its queries one after another
+    ppr = [r.source for r in reqs if r.algo == "ppr"]
+    assert lib.ctx["p"]["steps"] == sum((s % 5) + 1 for s in ppr)
