@@ -1,4 +1,6 @@
-"""Host logic of the serving loop (no GPU): the Poisson request generator, the latency statistics and the continuous-batching loop against a fake of the serving calls."""
+"""Host logic of the serving loop (no GPU): the Poisson request generator,
+the latency statistics, and the continuous-batching loop against a fake of
+the serving calls."""
 import numpy as np
 
 from paper_2208_14935_gb300.serve import poisson_requests, Request, latency_stats
