@@ -18,6 +18,7 @@ import collections
 import json
 import os
 import sys
+import threading
 import time
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional
@@ -49,24 +50,58 @@ class _Lane:
 
 
 class Server:
-    """Serve BFS/SSSP/PPR queries with continuous batching."""
+    """Serve BFS/SSSP/PPR queries with continuous batching.
+
+    threads=False: one host thread steps the engines in turn.  threads=True:
+    one host thread per engine (the ctypes calls release the interpreter
+    lock), so one engine's host-side waits do not hold back the others."""
 
     def __init__(self, engines: Dict[str, "hytg.Engine"], slots: Optional[Dict[str, int]] = None,
-                 keep_results: bool = True):
+                 keep_results: bool = True, threads: bool = False):
         self.lanes: Dict[str, _Lane] = {}
         self.keep_results = keep_results
+        self.threads = threads
         for algo, eng in engines.items():
             n = (slots or {}).get(algo, 32 if algo == "ppr" else 64)
             lane = _Lane(eng, algo, n, [None] * n)
             self.lanes[algo] = lane
+
+    def _admit(self, lane: _Lane, t0: float, clock) -> None:
+        for s in range(lane.slots):
+            if lane.occupant[s] is None and lane.waiting:
+                r = lane.waiting.popleft()
+                hytg.hytg_serve_admit(lane.eng.ctx, s, r.source)
+                r.admitted = clock() - t0
+                lane.occupant[s] = r
+
+    def _step(self, lane: _Lane, t0: float, clock) -> List[Request]:
+        """One iteration of the lane's engine; returns the queries it finished."""
+        fin, _ = hytg.hytg_serve_step(lane.eng.ctx)
+        lane.steps += 1
+        out = []
+        s = 0
+        while fin:
+            if fin & 1:
+                r = lane.occupant[s]
+                res = hytg.hytg_serve_fetch(lane.eng.ctx, s, lane.eng.V, hytg.ALGOS[lane.algo])
+                r.done = clock() - t0
+                if self.keep_results:
+                    r.result = res
+                lane.occupant[s] = None
+                out.append(r)
+            fin >>= 1
+            s += 1
+        return out
 
     def run(self, requests: List[Request], clock=time.perf_counter) -> List[Request]:
         for lane in self.lanes.values():
             hytg.hytg_serve_begin(lane.eng.ctx, hytg.ALGOS[lane.algo], lane.slots)
         todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
         t0 = clock()
-        done: List[Request] = []
         try:
+            if self.threads:
+                return self._run_threaded(todo, t0, clock)
+            done: List[Request] = []
             while todo or any(l.waiting or any(l.occupant) for l in self.lanes.values()):
                 now = clock() - t0
                 while todo and todo[0].arrival <= now:
@@ -74,36 +109,61 @@ class Server:
                     self.lanes[r.algo].waiting.append(r)
                 busy = False
                 for lane in self.lanes.values():
-                    for s in range(lane.slots):
-                        if lane.occupant[s] is None and lane.waiting:
-                            r = lane.waiting.popleft()
-                            hytg.hytg_serve_admit(lane.eng.ctx, s, r.source)
-                            r.admitted = clock() - t0
-                            lane.occupant[s] = r
+                    self._admit(lane, t0, clock)
                     if any(lane.occupant):
                         busy = True
-                        fin, _ = hytg.hytg_serve_step(lane.eng.ctx)
-                        lane.steps += 1
-                        s = 0
-                        while fin:
-                            if fin & 1:
-                                r = lane.occupant[s]
-                                res = hytg.hytg_serve_fetch(lane.eng.ctx, s, lane.eng.V,
-                                                            hytg.ALGOS[lane.algo])
-                                r.done = clock() - t0
-                                if self.keep_results:
-                                    r.result = res
-                                lane.occupant[s] = None
-                                done.append(r)
-                            fin >>= 1
-                            s += 1
+                        done.extend(self._step(lane, t0, clock))
                 if not busy and todo:
                     wait = todo[0].arrival - (clock() - t0)
                     if wait > 0:
                         time.sleep(min(wait, 0.01))
+            return done
         finally:
             for lane in self.lanes.values():
                 hytg.hytg_serve_end(lane.eng.ctx)
+
+    def _run_threaded(self, todo: collections.deque, t0: float, clock) -> List[Request]:
+        lock = threading.Lock()
+        done: List[Request] = []
+        left = collections.Counter(r.algo for r in todo)     # not yet admitted, per engine
+        errors: List[BaseException] = []
+
+        def lane_loop(lane: _Lane) -> None:
+            try:
+                while True:
+                    with lock:
+                        now = clock() - t0
+                        while todo and todo[0].arrival <= now:
+                            r = todo.popleft()
+                            self.lanes[r.algo].waiting.append(r)
+                        before = len(lane.waiting)
+                        self._admit(lane, t0, clock)
+                        left[lane.algo] -= before - len(lane.waiting)
+                        busy = any(lane.occupant)
+                        finished = not busy and left[lane.algo] == 0
+                        nxt = todo[0].arrival if todo else None
+                    if finished:
+                        return
+                    if busy:
+                        out = self._step(lane, t0, clock)
+                        if out:
+                            with lock:
+                                done.extend(out)
+                    elif nxt is not None:
+                        wait = nxt - (clock() - t0)
+                        time.sleep(min(max(wait, 0.0), 0.01) if wait > 0 else 0.0005)
+                    else:
+                        time.sleep(0.0005)
+            except BaseException as ex:             # surfaced after the join
+                errors.append(ex)
+
+        workers = [threading.Thread(target=lane_loop, args=(lane,)) for lane in self.lanes.values()]
+        for w in workers:
+            w.start()
+        for w in workers:
+            w.join()
+        if errors:
+            raise errors[0]
         return done
 
 
@@ -140,6 +200,7 @@ def _main():
     ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--n", type=int, default=200, help="requests per rate")
     ap.add_argument("--rates", default="0.25,0.5,0.9", help="fractions of the saturation rate")
+    ap.add_argument("--threads", action="store_true", help="one host thread per engine")
     ap.add_argument("--max-seconds", type=float, default=60.0,
                     help="cap on the arrival span of each rated run (fewer requests at low rates)")
     args = ap.parse_args()
@@ -165,7 +226,7 @@ def _main():
     cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
     rng = np.random.default_rng(3)
     pools = {a: rng.choice(cand, 4096, replace=True) for a in ("bfs", "sssp", "ppr")}
-    srv = Server(engines, keep_results=False)
+    srv = Server(engines, keep_results=False, threads=args.threads)
     # saturation: every request present at t = 0 (closed burst)
     warm = poisson_requests(min(64, args.n), float("inf"), pools, seed=9)
     srv.run(warm)
@@ -174,6 +235,7 @@ def _main():
     out = {"metric": "served queries: p50/p99 latency and queries/s (continuous batching)",
            "graph": {"family": args.graph, "V": g.V, "E": g.E, "gen_s": round(gen_s, 1)},
            "budget_bytes": budget, "mix": "BFS:SSSP:PPR = 2:2:1", "slots": {"bfs": 64, "sssp": 64, "ppr": 32},
+           "host_threads": 3 if args.threads else 1,
            "saturation": sat, "rates": {}}
     for frac in [float(x) for x in args.rates.split(",")]:
         rate = frac * sat["qps"]

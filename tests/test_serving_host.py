@@ -2,6 +2,7 @@
 the latency statistics, and the continuous-batching loop against a fake of
 the serving calls."""
 import numpy as np
+import pytest
 
 from paper_2208_14935_gb300.serve import poisson_requests, Request, latency_stats
 
@@ -64,7 +65,8 @@ class _FakeServeLib:
         self.ctx[ctx]["open"] = False
 
 
-def test_continuous_batching_loop(monkeypatch):
+@pytest.mark.parametrize("threads", [False, True])
+def test_continuous_batching_loop(monkeypatch, threads):
     from paper_2208_14935_gb300 import hytg
     from paper_2208_14935_gb300.serve import Server
 
@@ -81,7 +83,7 @@ def test_continuous_batching_loop(monkeypatch):
             self.V = 8
 
     engines = {"bfs": Eng("b"), "sssp": Eng("s"), "ppr": Eng("p")}
-    srv = Server(engines, slots={"bfs": 3, "sssp": 2, "ppr": 1})
+    srv = Server(engines, slots={"bfs": 3, "sssp": 2, "ppr": 1}, threads=threads)
     pools = {"bfs": np.arange(0, 40), "sssp": np.arange(40, 80), "ppr": np.arange(80, 120)}
     reqs = poisson_requests(60, float("inf"), pools, seed=2)     # all at t = 0: slots bound admission
     done = srv.run(reqs)
@@ -98,3 +100,28 @@ def test_continuous_batching_loop(monkeypatch):
     # the single-slot engine runs its queries one after another
     ppr = [r.source for r in reqs if r.algo == "ppr"]
     assert lib.ctx["p"]["steps"] == sum((s % 5) + 1 for s in ppr)
+
+
+def test_threaded_loop_with_arrivals_over_time(monkeypatch):
+    """Arrivals spread over time: every query is admitted after it arrives and
+    retired once, with one host thread per engine."""
+    from paper_2208_14935_gb300 import hytg
+    from paper_2208_14935_gb300.serve import Server
+
+    lib = _FakeServeLib()
+    for name in ("begin", "admit", "step", "fetch", "end"):
+        monkeypatch.setattr(hytg, f"hytg_serve_{name}", getattr(lib, name))
+
+    class Eng:
+        def __init__(self, name):
+            self.ctx = name
+            self.V = 4
+
+    srv = Server({"bfs": Eng("b"), "ppr": Eng("p")}, slots={"bfs": 2, "ppr": 2}, threads=True)
+    pools = {"bfs": np.arange(0, 10), "sssp": np.arange(0, 10), "ppr": np.arange(10, 20)}
+    reqs = poisson_requests(40, 2000.0, pools, mix=(("bfs", 1), ("ppr", 1)), seed=4)
+    done = srv.run(reqs)
+    assert sorted(r.rid for r in done) == list(range(40))
+    for r in done:
+        assert r.admitted >= r.arrival and r.done >= r.admitted
+        assert np.all(r.result == r.source)
