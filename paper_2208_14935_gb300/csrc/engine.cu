@@ -655,23 +655,23 @@ hytg_status ensure_batch(hytg_ctx *c, int mode) {
     return HYTG_OK;
 }
 
-// Issue planning for one iteration on s_main: counts, selection, summary
-// copy (-> ev_sum[buf]), binning (-> ev_bin), and the device-sized cache and
-// zero-copy relaxes.
 hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop);
 
+// Start mark of the next iteration record (timing on).
 void iteration_mark(hytg_ctx *c) {
     if (c->timing == 0) return;
     cudaEvent_t e = pool_event(c);
     if (cudaEventRecord(e, c->s_main) == cudaSuccess) c->iter_ev.push_back({c->iters.size(), e});
 }
 
+// Issue planning for one iteration on s_main: counts, selection, summary
+// copy (-> ev_sum[buf]) and, with work, binning (-> ev_bin) and the
+// device-sized cache and zero-copy relaxes (issue_plan_tail).
 hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, int buf, bool with_work) {
     if (with_work) iteration_mark(c);
     GraphDev g = graph_dev(c);
     AlgoState st = algo_state(c, algo, bucket);
     PartArrays pa = part_arrays(c);
-    ListArrays la = list_arrays(c);
     Summary *sum = (Summary *)c->d_sumbuf;
     const uint32_t N = g.N;
     if ((algo == kPR || algo == kPPR) && it > 0 && c->batch_mode == kBatchNone) {
