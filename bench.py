@@ -8,13 +8,17 @@ connected components on the symmetrised graph (536,870,912 edges) and
 delta-PageRank (damping 0.85, FP32 residual threshold 1e-9), each to
 convergence through the C ABI.
 
-value  = edges relaxed (sum over iterations of active out-edges, plus the
-         second-pass relaxations over resident partitions, Sec. VI-A) / device
-         time of the runs (CUDA events on the library's main stream, which
-         joins all of its streams), summed over the K timed steps, over all
-         ranks, divided by the slowest rank's time;
+value  = edges relaxed (sum over iterations of the active out-edges, the
+         algorithmic count, identical for every route) / device time of the
+         runs (CUDA events on the library's main stream, which joins all of
+         its streams), summed over the K timed steps, over all ranks, divided
+         by the slowest rank's time.  Second-pass re-relaxations over resident
+         partitions (Sec. VI-A) depend on the schedule and are reported beside
+         it (config.gteps_with_second_pass), not in it;
 e2e    = the same edges over host wall time of hytg_run + hytg_fetch_result
          (the public calls), including the result copies to host memory.
+The host-link denominator is the pinned-memcpy probe measured in the same
+process before and after the timed steps (their mean).
 
 Multi-GPU: replicas only (each rank runs the whole workload on its own GPU;
 no data-path collective); the barrier and max-over-ranks timing use
@@ -206,21 +210,41 @@ def batched_vs_plain(hytg, eng, g, n_plain_sssp=16, n_plain_ppr=4):
 
 
 # ------------------------------------------------------- reference arm ----
-def cpu_oracle_sample(g, budget_s: float = 20.0):
-    """The oracle (plain single-threaded C) on a bounded sample: BFS from 0,
-    then Dijkstra from 0 if the BFS left time in the budget."""
+def oracle_sample(name, g, s):
+    """One oracle run on the host cores (plain single-threaded C) on the full
+    graph: FIFO BFS or Dijkstra from vertex 0, union-find CC on the
+    symmetrised graph, or one FP64 power-iteration sweep of PageRank (the full
+    solve takes over a hundred sweeps).  Returns (edges processed, seconds)."""
     from oracle import oracle as orc
     t0 = time.perf_counter()
-    _, e_bfs = orc.bfs(g, 0)
-    t1 = time.perf_counter()
-    edges, secs, sample = e_bfs, t1 - t0, "oracle BFS from vertex 0 on the full graph"
-    if (t1 - t0) * 6 < budget_s:
-        _, e_sp, _ = orc.sssp(g, 0)
-        t2 = time.perf_counter()
-        edges += e_sp
-        secs = t2 - t0
-        sample += " + oracle Dijkstra from vertex 0 on the full graph"
-    return edges, secs, sample
+    if name == "bfs":
+        _, e = orc.bfs(g, 0)
+    elif name == "sssp":
+        _, e, _ = orc.sssp(g, 0)
+    elif name == "cc":
+        orc.cc(s)
+        e = s.E
+    else:
+        orc.pagerank(g, maxit=1)
+        e = g.E
+    return int(e), time.perf_counter() - t0
+
+
+ORACLE_WHAT = {"bfs": "FIFO BFS from vertex 0", "sssp": "Dijkstra from vertex 0",
+               "cc": "union-find CC on the symmetrised graph",
+               "pagerank": "one FP64 PageRank power-iteration sweep"}
+
+
+def cpu_oracle_samples(g, s, algos, budget_s: float = 25.0):
+    """Each algorithm of the step once through the oracle, while the budget lasts."""
+    out, used = {}, 0.0
+    for a in algos:
+        if used > budget_s:
+            break
+        e, dt = oracle_sample(a, g, s)
+        used += dt
+        out[a] = {"edges": e, "s": round(dt, 3), "gteps": e / dt / 1e9, "what": ORACLE_WHAT[a]}
+    return out
 
 
 def step_config(args, g, s, algos, world):
@@ -236,30 +260,41 @@ def step_config(args, g, s, algos, world):
 
 
 def run_reference(args):
+    """The oracle as the CPU reference: every step runs one algorithm of the
+    GPU step on the full graph, in turn (BFS, Dijkstra, union-find CC, one
+    PageRank sweep), so the timed steps sample all four; value = edges
+    processed / seconds over the timed steps."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     g, s = make_graphs(args.scale)
     from oracle import oracle as orc
     orc.build()
+    algos = [a for a in args.algos.split(",") if a]
     total_e, total_s = 0, 0.0
-    sample = ""
+    per = {}
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        lv, e = orc.bfs(g, 0)
-        dt = time.perf_counter() - t0
-        sample = "oracle FIFO BFS from vertex 0 on the full graph, one per step"
+        a = algos[(i - args.warmup) % len(algos)]
+        e, dt = oracle_sample(a, g, s)
         if i >= args.warmup:
             total_e += e
             total_s += dt
+            p = per.setdefault(a, {"edges": 0, "s": 0.0, "steps": 0})
+            p["edges"] += e
+            p["s"] += dt
+            p["steps"] += 1
     v = total_e / total_s / 1e9
+    for p in per.values():
+        p["gteps"] = p["edges"] / p["s"] / 1e9
+    sample = ("oracle (single-threaded C) on the full graph, one algorithm per step in turn: " +
+              ", ".join(ORACLE_WHAT[a] for a in algos))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (PageRank f64)",
             "data": "synthetic",
-            "config": step_config(args, g, s, [a for a in args.algos.split(",") if a], 1),
+            "config": step_config(args, g, s, algos, 1),
             "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "per_algo": per, "host_cores": os.cpu_count()},
             "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -336,6 +371,46 @@ def run_mesh_only(args):
     print(json.dumps(line), flush=True)
 
 
+U64_MAX = (1 << 64) - 1
+LINK_KINDS = (5, 7, 8)          # C gathers, Z relaxes, F copies: the launches that move host-link bytes
+
+
+def union_ms(iv):
+    """Total length of the union of intervals [(start, end), ...]."""
+    busy, lo, hi = 0.0, 0.0, -1.0
+    for a, b in sorted(iv):
+        if a > hi:
+            if hi > lo:
+                busy += hi - lo
+            lo, hi = a, b
+        elif b > hi:
+            hi = b
+    if hi > lo:
+        busy += hi - lo
+    return busy
+
+
+def timeline_summary(tl, hytg):
+    """Per-run figures from the launch timeline: every F copy's rate, the wall
+    time during which any route moved host-link bytes, and per-launch edge
+    counts and durations of the two PageRank kernels."""
+    dur = tl["end_ms"] - tl["start_ms"]
+    cp = tl["kind"] == 8
+    link = np.isin(tl["kind"], LINK_KINDS)
+    sp = (tl["kind"] == hytg.K_SECOND_PASS) & (tl["edges"] != U64_MAX)
+    rf = tl["kind"] == 4
+    return {"copy_gbs": (tl["bytes"][cp] / np.maximum(dur[cp], 1e-6) / 1e6).tolist(),
+            "copy_stream": tl["stream"][cp].tolist(),
+            "link_busy_ms": union_ms(list(zip(tl["start_ms"][link], tl["end_ms"][link]))),
+            "sp_n": int(sp.sum()), "sp_ms": float(dur[sp].sum()), "sp_edges": int(tl["edges"][sp].sum()),
+            "sp_vertices": int(tl["vertices"][sp].sum()),
+            "rf_n": int(rf.sum()), "rf_ms": float(dur[rf].sum()), "rf_edges": int(tl["edges"][rf].sum())}
+
+
+def pct(xs, q):
+    return float(np.percentile(xs, q)) if len(xs) else None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -366,8 +441,9 @@ def main():
         params[k] = float(v)
     eng = hytg.Engine(g, budget=int(args.budget_frac * graph_bytes), device=local, params=params)
     eng_s = hytg.Engine(s, budget=int(args.budget_frac * sym_bytes), device=local, params=params)
+    damping = eng.get_param("pr_damping")
 
-    def one_step(collect):
+    def one_step():
         per = {}
         for algo in algos:
             e = eng_s if algo == "cc" else eng
@@ -377,162 +453,138 @@ def main():
             out = hytg.hytg_fetch_result(e.ctx, e.V, hytg.ALGOS[algo])
             wall = (time.perf_counter() - t0) * 1e3
             st = e.stats()
+            tl = timeline_summary(e.timeline(), hytg) if not args.no_timing else None
             per[algo] = {"stats": st, "wall_ms": wall, "d2h": out.nbytes,
-                         "h2d": 0 if src is None else 4}
+                         "h2d": 0 if src is None else 4, "tl": tl}
         return per
 
+    # the link denominator, measured in this process before and after the timed steps
+    probe_before = None if args.no_probe else eng.probe_link(1 << 30, 10)
     for _ in range(args.warmup):
-        one_step(False)
+        one_step()
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
-    steps = []
-    for _ in range(args.steps):
-        steps.append(one_step(True))
+    steps = [one_step() for _ in range(args.steps)]
     barrier(world)
     clk = clocks.stop()
+    probe_after = None if args.no_probe else eng.probe_link(1 << 30, 10)
     batched = None if args.no_batched else batched_vs_plain(hytg, eng, g)
     red_probe = None if args.no_probe else eng.probe_atomics(1 << 28, 5)
-    # the link probe runs after the timed region (it pins and frees 1 GiB)
-    memcpy_gbs, zc_gbs = (float("nan"), float("nan")) if args.no_probe else eng.probe_link(1 << 30, 10)
+    probe = float("nan") if args.no_probe else (probe_before[0] + probe_after[0]) / 2
 
-    # every relaxation of an active vertex's out-edges: planned iterations plus
-    # the second passes over resident partitions (Sec. VI-A, on for PageRank)
-    edges = sum(p[a]["stats"]["edges_relaxed"] + p[a]["stats"]["extra_edges"] for p in steps for a in algos)
-    dev_ms = sum(p[a]["stats"]["device_ms"] for p in steps for a in algos)
+    def tot(a, key, i=None):
+        return sum((p[a]["stats"][key] if i is None else p[a]["stats"][key][i]) for p in steps)
+
+    # TEPS numerator: active out-edges relaxed over the iterations (the
+    # algorithmic count, the same for every route); second-pass re-relaxations
+    # over resident partitions are reported beside it, not in it
+    edges = sum(tot(a, "edges_relaxed") for a in algos)
+    extra = sum(tot(a, "extra_edges") for a in algos)
+    dev_ms = sum(tot(a, "device_ms") for a in algos)
     wall_ms = sum(p[a]["wall_ms"] for p in steps for a in algos)
-    launches = sum(p[a]["stats"]["kernel_launches"] for p in steps for a in algos)
+    launches = sum(tot(a, "kernel_launches") for a in algos)
     tot_edges, max_ms = aggregate(float(edges), dev_ms, world)
     tot_edges_w, max_wall = aggregate(float(edges), wall_ms, world)
     value = tot_edges / (max_ms * 1e-3) / 1e9
     e2e = tot_edges_w / (max_wall * 1e-3) / 1e9
 
-    # host link: bytes moved over the link by the F, C and Z routes / device time
-    link_bytes = sum(sum(p[a]["stats"]["link_bytes"]) for p in steps for a in algos)
-    link_gbs = link_bytes / (dev_ms * 1e-3) / 1e9
-    # per route: its bytes over the time its transfers were in flight (union
-    # over streams of the F copies / C gathers / Z relaxes, timing on)
+    # host link: F bytes copied, C/Z sectors the kernels read from host memory
+    link_bytes = sum(tot(a, "link_sector_bytes", r) for a in algos for r in range(5))
+    model_bytes = sum(tot(a, "link_bytes", r) for a in algos for r in range(5))
     per_route = {}
     for r, name in ((2, "F"), (3, "C"), (4, "Z")):
-        b = sum(p[a]["stats"]["link_bytes"][r] for p in steps for a in algos)
-        busy = sum(p[a]["stats"]["route_busy_ms"][r] for p in steps for a in algos)
-        per_route[name] = {"bytes": b, "busy_ms": round(busy, 2),
-                           "gbs": b / (busy * 1e-3) / 1e9 if busy > 0 else None}
+        b = sum(tot(a, "link_sector_bytes", r) for a in algos)
+        busy = sum(tot(a, "route_busy_ms", r) for a in algos)
+        per_route[name] = {"bytes": b, "model_line_bytes": sum(tot(a, "link_bytes", r) for a in algos),
+                           "busy_ms": round(busy, 2),
+                           "frac_of_probe": (b / (busy * 1e-3) / 1e9 / probe) if busy > 0 else None}
     per_algo = {}
     for a in algos:
-        ed = sum(p[a]["stats"]["edges_relaxed"] + p[a]["stats"]["extra_edges"] for p in steps)
-        ms = sum(p[a]["stats"]["device_ms"] for p in steps)
+        ed, ms = tot(a, "edges_relaxed"), tot(a, "device_ms")
+        ex = tot(a, "extra_edges")
+        lb = sum(tot(a, "link_sector_bytes", r) for r in range(5))
         st = steps[-1][a]["stats"]
-        kk = [sum(p[a]["stats"]["kernel_ms"][i] for p in steps) / len(steps) for i in range(12)]
-        per_algo[a] = {"gteps": ed / (ms * 1e-3) / 1e9, "ms": ms / len(steps),
-                       "ms_each_step": [round(p[a]["stats"]["device_ms"], 2) for p in steps],
-                       "kernel_ms": {hytg.KERNEL_KINDS[i]: round(kk[i], 2) for i in range(12) if kk[i]},
-                       "iterations": st["iterations"], "edges_relaxed": st["edges_relaxed"],
-                       "second_pass_edges": st["extra_edges"],
-                       "second_pass_ms": round(sum(p[a]["stats"]["second_pass_ms"] for p in steps) / len(steps), 2),
-                       "graph_iterations": st["graph_iterations"],
-                       "route_partitions": dict(zip(hytg.ROUTE_NAMES, st["route_partitions"])),
-                       "route_edges": dict(zip(hytg.ROUTE_NAMES, st["route_edges"])),
-                       "link_bytes": sum(st["link_bytes"])}
+        d = {"gteps": ed / (ms * 1e-3) / 1e9, "ms": round(ms / len(steps), 2),
+             "link_gbs": lb / (ms * 1e-3) / 1e9, "link_frac": lb / (ms * 1e-3) / 1e9 / probe,
+             "iterations": st["iterations"], "graph_iterations": st["graph_iterations"],
+             "edges_relaxed": st["edges_relaxed"]}
+        if ex:
+            d["second_pass_edges"] = st["extra_edges"]
+            d["gteps_with_second_pass"] = (ed + ex) / (ms * 1e-3) / 1e9
+        if not args.no_timing:
+            busy = sum(p[a]["tl"]["link_busy_ms"] for p in steps)
+            d["link_busy_frac"] = busy / ms
+            d["link_frac_while_busy"] = lb / (busy * 1e-3) / 1e9 / probe if busy > 0 else None
+        if a == "pagerank":
+            # a-posteriori bound on the L1 error of the normalised ranks:
+            # sum |delta| left / ((1 - d) * sum rank)
+            d["l1_bound"] = st["pr_residual_sum"] / ((1 - damping) * st["pr_rank_sum"])
+        per_algo[a] = d
 
-    # dominant kernel kind over the timed steps (per-kind CUDA events)
-    kinds = hytg.KERNEL_KINDS
-    kms = [0.0] * 12
-    kcnt = [0] * 12
-    for p in steps:
-        for a in algos:
-            for i in range(12):
-                kms[i] += p[a]["stats"]["kernel_ms"][i]
-                kcnt[i] += p[a]["stats"]["kernel_count"][i]
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roofline, roofline_l2, roofline_relax = None, None, None
+    roofline, roofline_l2 = None, None
     if not args.no_timing and "pagerank" in algos:
-        # PageRank is most of the step.  Its two heaviest kernels in the ncu
-        # launch list (profiles/) are the second pass over resident partitions
-        # (k_second_pass<PageRank>, ~50-60 %) and the F-route relax
-        # (k_relax<PageRank>, ~20-30 %); `roofline` is whichever took longer
-        # in this run, the other is reported beside it.
-        pr = [p["pagerank"]["stats"] for p in steps]
-        ms_f = sum(st["kernel_ms"][4] for st in pr)
-        n_f = sum(st["kernel_count"][4] for st in pr)
-        e_f = sum(st["route_edges"][2] for st in pr)
-        v_f = sum(st["route_vertices"][2] for st in pr)
-        busy_f = sum(st["kernel_busy_ms"][4] for st in pr)
-        busy_sp = sum(st["kernel_busy_ms"][12] for st in pr)
-        ms_sp = sum(st["second_pass_ms"] for st in pr)
-        n_sp = sum(st["second_pass_count"] for st in pr)
-        e_sp = sum(st["extra_edges"] for st in pr)
-        v_sp = sum(st["second_pass_vertices"] for st in pr)
-        if ms_f > 0 and n_f > 0:
-            # algorithmic bytes: 4 B edge + 8 B value read-modify-write per edge,
-            # 20 B list entry per active vertex
-            alg = e_f * 12 + v_f * 20
-            achieved = alg / (ms_f * 1e-3) / 1e9
-            # DRAM bytes per launch from the ncu capture of the same kernel on an
-            # F task of the same size (profiles/k_relax_pagerank_rmat22.md):
-            # 30.8 MB for 4.37 M edges, scaled by this run's edges per launch
-            traffic = 30.8e6 / 4.37e6 * (e_f / n_f)
-            roofline_relax = {"kernel": "k_relax<PageRank> F route", "bound": "hbm", "achieved": achieved,
-                              "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                              "bytes_model": "per edge 4 + 8 (value RMW), per active vertex 20",
-                              "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                              "launches": n_f, "avg_launch_us": ms_f * 1e3 / n_f,
-                              "alg_bytes_per_launch": alg / n_f,
-                              # the same bytes over the wall time during which any F
-                              # relax was running (launches overlap on 4 streams)
-                              "achieved_while_running": alg / (busy_f * 1e-3) / 1e9 if busy_f else None}
-        if ms_sp > 0 and n_sp > 0:
-            # per edge 4 B edge + 8 B value RMW; per scanned vertex 16 B offsets,
-            # 4 B delta read, 8 B delta and rank reductions
-            alg = e_sp * 12 + v_sp * 28
-            achieved = alg / (ms_sp * 1e-3) / 1e9
-            rl_sp = {"kernel": "k_second_pass<PageRank>", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "traffic_note": "not captured for a launch of known size; a cold-cache capture of "
-                                     "one R-MAT 22 launch read 55.5 MB (profiles/)",
-                     "bytes_model": "per edge 4 + 8 (value RMW), per scanned vertex 28",
-                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                     "launches": n_sp, "avg_launch_us": ms_sp * 1e3 / n_sp,
-                     "alg_bytes_per_launch": alg / n_sp,
-                     "achieved_while_running": alg / (busy_sp * 1e-3) / 1e9 if busy_sp else None}
-            if roofline_relax is None or ms_sp > ms_f:
-                roofline, roofline_relax = rl_sp, roofline_relax
-            else:
-                roofline, roofline_relax = roofline_relax, rl_sp
-        else:
-            roofline, roofline_relax = roofline_relax, None
-        if red_probe and ms_f > 0:
-            rate = e_f / (ms_f * 1e-3) / 1e9
-            roofline_l2 = {"kernel": "k_relax<PageRank> F route", "bound": "l2_reductions",
-                           "achieved": rate, "peak": red_probe[0], "unit": "G updates/s",
-                           "frac": rate / red_probe[0],
-                           "achieved_while_running": e_f / (busy_f * 1e-3) / 1e9 if busy_f else None,
-                           "peak_source": "hytg_probe_atomics, uniform targets, same run",
-                           "skewed_targets_gops": red_probe[1]}
-    elif not args.no_timing:
-        relax = {"relax_Z": 7, "relax_cache": 3, "relax_F": 4, "relax_C": 6, "gather_C": 5}
-        dom = max(relax, key=lambda k: kms[relax[k]])
-        route_of = {"relax_Z": 4, "relax_cache": 1, "relax_F": 2, "relax_C": 3, "gather_C": 3}
-        r = route_of[dom]
-        alg_bytes = 0
-        for p in steps:
-            for a in algos:
-                d1 = 8 if a == "sssp" else 4
-                st = p[a]["stats"]
-                alg_bytes += st["route_edges"][r] * (d1 + 8) + st["route_vertices"][r] * 20
-        ms = kms[relax[dom]]
-        achieved = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None,
-                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+        # PageRank is most of the step; its two heaviest kernels are the second
+        # pass over resident partitions and the F-route relax.  Per launch from
+        # the timeline (CUDA events on the launching stream, timed region only).
+        tls = [p["pagerank"]["tl"] for p in steps]
+        prs = [p["pagerank"]["stats"] for p in steps]
+        sp_n, sp_ms = sum(t["sp_n"] for t in tls), sum(t["sp_ms"] for t in tls)
+        sp_e, sp_v = sum(t["sp_edges"] for t in tls), sum(t["sp_vertices"] for t in tls)
+        rf_n, rf_ms = sum(t["rf_n"] for t in tls), sum(t["rf_ms"] for t in tls)
+        rf_e = sum(t["rf_edges"] for t in tls)
+        rf_v = sum(st["route_vertices"][2] for st in prs)
+        kern = {}
+        if sp_n:
+            # per relaxed edge 4 B edge + 8 B value read-modify-write; per
+            # scanned vertex 16 B offsets, 4 B delta read, 8 B delta and rank updates
+            kern["k_second_pass<PageRank>"] = (sp_n, sp_ms, sp_e, sp_e * 12 + sp_v * 28,
+                                               "per edge 4 + 8 (value RMW), per scanned vertex 28")
+        if rf_n:
+            # per edge 4 B edge + 8 B RMW, per list entry 20 B
+            kern["k_relax<PageRank> F route"] = (rf_n, rf_ms, rf_e, rf_e * 12 + rf_v * 20,
+                                                 "per edge 4 + 8 (value RMW), per active vertex 20")
+        if kern:
+            dom = max(kern, key=lambda k: kern[k][1])
+            n, ms, e_, alg, model = kern[dom]
+            achieved = alg / (ms * 1e-3) / 1e9
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm, "traffic": None,
+                        "traffic_note": "no ncu DRAM capture of the current kernel",
+                        "bytes_model": model, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                        "launches": n, "avg_launch_us": ms * 1e3 / n, "alg_bytes_per_launch": alg / n,
+                        "edges_per_launch": e_ / n,
+                        "binding_roof": "L2 reductions (roofline_l2): the value arrays stay in L2"}
+            if red_probe:
+                roofline_l2 = {}
+                for k, (n, ms, e_, _, _) in kern.items():
+                    rate = e_ / (ms * 1e-3) / 1e9
+                    roofline_l2[k] = {"bound": "l2_reductions", "achieved": rate, "peak": red_probe[0],
+                                      "unit": "G updates/s", "frac": rate / red_probe[0],
+                                      "frac_of_skewed_probe": rate / red_probe[1]}
+                roofline_l2["peak_source"] = ("hytg_probe_atomics in this run: uniform targets (peak), "
+                                              "R-MAT-skewed targets")
+                roofline_l2["skewed_gops"] = red_probe[1]
+                # all PageRank reductions over its device time (kernels overlap on 5 streams)
+                pr_e = sum(st["edges_relaxed"] + st["extra_edges"] for st in prs)
+                pr_ms = sum(st["device_ms"] for st in prs)
+                roofline_l2["pagerank_aggregate_gops"] = pr_e / (pr_ms * 1e-3) / 1e9
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        e_cpu, s_cpu, sample = cpu_oracle_sample(g)
+        smp = cpu_oracle_samples(g, s, algos)
+        e_cpu = sum(v["edges"] for v in smp.values())
+        s_cpu = sum(v["s"] for v in smp.values())
         cpu = {"value": e_cpu / s_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": sample, "seconds": s_cpu, "host_cores": os.cpu_count()}
+               "sample": "oracle (single-threaded C) on the full graphs, once each: " +
+                         ", ".join(v["what"] for v in smp.values()),
+               "seconds": round(s_cpu, 2), "host_cores": os.cpu_count(),
+               "per_algo": {a: {"cpu_gteps": v["gteps"], "gpu_gteps": per_algo[a]["gteps"],
+                                "cpu_s": v["s"]} for a, v in smp.items()}}
 
+    copy_gbs = [x for p in steps for a in algos if p[a]["tl"] for x in p[a]["tl"]["copy_gbs"]]
     h2d = sum(p[a]["h2d"] for p in steps for a in algos) // len(steps)
     d2h = sum(p[a]["d2h"] for p in steps for a in algos) // len(steps)
     link_per_step = link_bytes // len(steps)
@@ -540,27 +592,32 @@ def main():
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 (PageRank f32)", "data": "synthetic",
-        "config": dict(step_config(args, g, s, algos, world), graph_gen_s=round(t_gen, 1)),
-        "host_link": {"achieved_gbs": link_gbs, "memcpy_probe_gbs": memcpy_gbs,
-                      "zerocopy_probe_gbs": zc_gbs, "frac_of_measured": link_gbs / memcpy_gbs,
-                      "bytes_per_step": link_per_step,
-                      "while_transferring": {k: dict(v, frac_of_measured=(v["gbs"] / memcpy_gbs
-                                                                         if v["gbs"] else None))
-                                             for k, v in per_route.items()}},
-        "batched_vs_plain": batched,
+        "config": dict(step_config(args, g, s, algos, world), graph_gen_s=round(t_gen, 1),
+                       gteps_with_second_pass=(tot_edges + extra) / (max_ms * 1e-3) / 1e9,
+                       per_algo_gteps={a: round(v["gteps"], 2) for a, v in per_algo.items()},
+                       per_algo_ms={a: v["ms"] for a, v in per_algo.items()},
+                       pagerank_l1_bound=per_algo.get("pagerank", {}).get("l1_bound"),
+                       link_frac_of_probe=(link_bytes / (dev_ms * 1e-3) / 1e9 / probe)),
         "roofline": roofline,
-        "roofline_l2": roofline_l2,
-        "roofline_other": roofline_relax,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d + link_per_step,
                 "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline_l2": roofline_l2,
+        "batched_vs_plain": batched,
         # Graph500-style BFS rate: each reached vertex's out-edges are relaxed
         # exactly once, so the BFS edge count is |E_reached|
         "graph500_bfs_gteps": (per_algo["bfs"]["gteps"] if "bfs" in per_algo else None),
-        "gpu_launches": launches,
-        "clocks": clk,
+        "host_link": {"achieved_gbs": link_bytes / (dev_ms * 1e-3) / 1e9,
+                      "probe_before_gbs": probe_before[0] if probe_before else None,
+                      "probe_after_gbs": probe_after[0] if probe_after else None,
+                      "zerocopy_probe_gbs": probe_before[1] if probe_before else None,
+                      "frac_of_probe": link_bytes / (dev_ms * 1e-3) / 1e9 / probe,
+                      "bytes_per_step": link_per_step, "model_line_bytes_per_step": model_bytes // len(steps),
+                      "f_copy_gbs_p10_p50_p90": [pct(copy_gbs, q) for q in (10, 50, 90)],
+                      "while_transferring": per_route},
         "per_algo": per_algo,
-        "kernel_ms": {kinds[i]: kms[i] for i in range(12) if kcnt[i]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -51,7 +51,8 @@ typedef enum {
 typedef enum {
     HYTG_BFS = 0,       /* level[v]: hops from the source (Sec. VII-A)            */
     HYTG_SSSP = 1,      /* dist[v]: min sum of uint32 weights (Sec. II-A, Fig. 1)  */
-    HYTG_CC = 2,        /* label[v]: min vertex id of v's component; needs a symmetric CSR */
+    HYTG_CC = 2,        /* label[v]: min vertex id of v's component; needs a symmetric CSR
+                           (see hytg_run) */
     HYTG_PAGERANK = 3,  /* delta-based PageRank (Sec. VI-A), ranks normalised to sum 1 */
     HYTG_PPR = 4        /* personalised PageRank from one seed, normalised to sum 1 */
 } hytg_algo;
@@ -115,13 +116,21 @@ typedef struct hytg_stats {
     double kernel_busy_ms[13];        /* timing on: union over streams of the launches of
                                          each HYTG_K_* kind (index 12: the second pass), i.e.
                                          the wall time during which that kind was running */
+    uint64_t link_sector_bytes[5];    /* host-link bytes read, counted by the kernels that
+                                         read mapped host memory (Z relaxes, C gathers): in
+                                         each 2,048-edge tile, the distinct 32-byte sectors
+                                         its edges occupy, times 32 and the arrays read; F
+                                         (and C with "compact_host"): the bytes copied;
+                                         cache 0.  Index: hytg_route */
+    uint64_t link_line_bytes[5];      /* the same count at 128-byte lines, times 128 */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
 enum {
     HYTG_K_INIT = 0, HYTG_K_COUNT = 1, HYTG_K_BIN = 2, HYTG_K_RELAX_CACHE = 3,
     HYTG_K_RELAX_F = 4, HYTG_K_GATHER_C = 5, HYTG_K_RELAX_C = 6, HYTG_K_RELAX_Z = 7,
-    HYTG_K_COPY_F = 8, HYTG_K_FINAL = 9, HYTG_K_CACHE_FILL = 10, HYTG_K_OTHER = 11
+    HYTG_K_COPY_F = 8, HYTG_K_FINAL = 9, HYTG_K_CACHE_FILL = 10, HYTG_K_OTHER = 11,
+    HYTG_K_SECOND_PASS = 12           /* timeline only: a second pass (Sec. VI-A) */
 };
 
 /* Sizes and placement after load / budget / the last plan. */
@@ -131,7 +140,7 @@ typedef struct hytg_info {
     uint32_t n_parts;                 /* partitions of the edge arrays (Sec. IV) */
     uint64_t part_edges;              /* target edges per partition */
     uint64_t slot_edges;              /* edges per staging slot (k partitions) */
-    uint32_t n_slots;                 /* staging slots = F streams in use */
+    uint32_t n_slots;                 /* staging slots (F streams plus "prefetch_slots") */
     uint32_t n_cached;                /* partitions [0, n_cached) resident for the last algo */
     uint64_t budget_bytes;            /* device budget for edge-side data */
     uint64_t budget_used_bytes;       /* cache + staging + compaction buffer */
@@ -166,7 +175,10 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
 /* Set a tunable.  Keys: "alpha", "beta", "gamma" (Sec. V-A selection and
  * RTT_zc, stored as multiples of 1e-6), "m" (request bytes), "MR" (outstanding
  * requests), "k" (partitions per F task, Sec. V-B), "part_bytes" (partition
- * size in bytes of 4-byte entries, Sec. V-B), "streams" (F streams/slots),
+ * size in bytes of 4-byte entries, Sec. V-B), "streams" (F compute streams),
+ * "prefetch_slots" (staging slots beyond one per F stream, default 2: each
+ * slot has its own copy stream, so later tasks' copies run while earlier
+ * tasks still hold their slots),
  * "staging_frac", "compact_frac" (shares of the budget), "force_route"
  * (-1 cost model, 1 cache, 2 F, 3 C, 4 Z, 5 random per partition per
  * iteration), "seed" (for force_route 5), "pr_damping", "pr_eps" (FP32
@@ -194,7 +206,9 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * run ends; 0: the host drives every iteration.  Iterations run in the
  * graph report no per-iteration device time and are not in kernel_ms; if
  * the installed CUDA driver cannot build the graph, the context keeps using
- * the host loop and graph_launches stays 0).
+ * the host loop and graph_launches stays 0), "serve_frames" (serving:
+ * cap on the query frames hytg_serve_begin plans, 0 (default): as many as
+ * the slots can use; see hytg_serve_get_info).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);
@@ -208,8 +222,13 @@ hytg_status hytg_get_param(hytg_ctx *ctx, const char *key, double *value);
  * frontiers, so every partition transfer serves all sources at once (BFS:
  * 64-bit source masks per vertex; SSSP and PPR: one warp per edge with a lane
  * per source); delta-stepping is not used in batched SSSP.  The result stays
- * on the device until hytg_fetch_result.  Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no
- * budget), HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_CUDA. */
+ * on the device until hytg_fetch_result.  CC computes weakly connected
+ * components and needs a symmetric CSR: every edge u->v has a reverse v->u
+ * with the same multiplicity (a self-loop is its own reverse); the first CC
+ * run after a load checks this on the host (O(E) plus a sort of each row,
+ * cached with the graph) and an asymmetric graph gives HYTG_ERR_ARG.
+ * Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no budget),
+ * HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_CUDA. */
 hytg_status hytg_run(hytg_ctx *ctx, hytg_algo algo, const uint32_t *sources, uint32_t n_sources);
 
 /* Copy the last run's result into caller-owned host memory `out` of
@@ -273,6 +292,15 @@ hytg_status hytg_probe_link(hytg_ctx *ctx, uint64_t bytes, uint32_t reps, double
 hytg_status hytg_probe_atomics(hytg_ctx *ctx, uint64_t n, uint32_t reps, double *uniform_gops,
                                double *skewed_gops);
 
+/* The same reduction probe with the R-MAT in-degree skew after hub sorting
+ * (ids ordered by probability, hot ids first, as hytg_load_csr relabels
+ * them): additions straight into the 2^24 floats (*plain_gops), and with the
+ * relax kernels' scheme, where additions to ids below n_rep go to the
+ * issuing SM's row of per-SM replicas (*replica_gops; the rows are not
+ * folded).  n in [1024, 2^30], n_rep <= 2^20.  Allocates device memory. */
+hytg_status hytg_probe_atomics_hub(hytg_ctx *ctx, uint64_t n, uint32_t reps, uint32_t n_rep,
+                                   double *plain_gops, double *replica_gops);
+
 /* Per-iteration record of the last run (up to cap records). */
 typedef struct hytg_iter_record {
     uint64_t active_vertices;
@@ -285,6 +313,25 @@ typedef struct hytg_iter_record {
                                          the next one's (timing parameter 1), else 0 */
 } hytg_iter_record;
 hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t cap, uint32_t *n);
+
+/* One timed launch or copy of the last hytg_run ("timing" parameter 1), in
+ * issue order.  Host-issued work only: iterations inside the device-loop
+ * graph are not split into launches.  The second-pass entries, in order, are
+ * the process's k_second_pass launches of that run, so a profiler's launch
+ * index can be matched to its edge count when the device loop is off. */
+typedef struct hytg_timed_launch {
+    uint32_t kind;                    /* HYTG_K_* (HYTG_K_SECOND_PASS for a second pass) */
+    uint32_t stream;                  /* 0 main stream, 1 compaction stream, 2 + i F stream i,
+                                         10 + j copy stream of staging slot j */
+    double start_ms, end_ms;          /* CUDA-event times from the run's start event */
+    uint64_t bytes;                   /* HYTG_K_COPY_F, host-compaction chunks: bytes copied */
+    uint64_t edges;                   /* HYTG_K_RELAX_F: active edges of the task;
+                                         HYTG_K_SECOND_PASS: edges it relaxed (UINT64_MAX when
+                                         more than 16,382 second passes ran and the later ones
+                                         share a counter) */
+    uint64_t vertices;                /* HYTG_K_SECOND_PASS: vertices of the range it scanned */
+} hytg_timed_launch;
+hytg_status hytg_get_timeline(hytg_ctx *ctx, hytg_timed_launch *out, uint32_t cap, uint32_t *n);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching over a batched run.  hytg_serve_begin opens a
@@ -301,10 +348,36 @@ hytg_status hytg_get_iterations(hytg_ctx *ctx, hytg_iter_record *out, uint32_t c
  * iteration, so their work overlaps on the device; a query's result does not
  * depend on the others.  hytg_run is refused while serving. */
 hytg_status hytg_serve_begin(hytg_ctx *ctx, hytg_algo algo, uint32_t n_slots);
+/* hytg_serve_admit: HYTG_ERR_BUDGET when the slot's group of 8 has no frame
+ * of device memory and none is free (see hytg_serve_get_info). */
 hytg_status hytg_serve_admit(hytg_ctx *ctx, uint32_t slot, uint32_t source);
 hytg_status hytg_serve_step(hytg_ctx *ctx, uint64_t *finished, uint64_t *busy);
 hytg_status hytg_serve_fetch(hytg_ctx *ctx, uint32_t slot, void *out, uint64_t out_bytes);
 hytg_status hytg_serve_end(hytg_ctx *ctx);
+
+/* Device memory of the open serving run.  A serving run's budget (the one
+ * hytg_set_device_budget set) holds both the edge-side data (cache, staging,
+ * compaction buffer) and the queries' per-source state, in frames of 8
+ * queries: slots [8 g, 8 g + 8) share frame memory (BFS/SSSP V * 32 bytes,
+ * PPR V * 96 bytes), attached when the group's first query is admitted and
+ * released when its last one is fetched.  hytg_serve_begin plans as many
+ * frames as the slots can use (at most the "serve_frames" parameter, when it
+ * is nonzero), fewer if the budget cannot hold them beside the smallest
+ * edge-side carve (HYTG_ERR_BUDGET if it holds none); the edge side gets the
+ * rest.  hytg_serve_admit returns HYTG_ERR_BUDGET, and admits nothing, when
+ * the slot's group has no frame and none is free: the query waits for memory
+ * even though the slot is free.  Masks and list arrays that do not grow with
+ * the number of queries are vertex-side data, outside the budget. */
+typedef struct hytg_serve_info {
+    uint32_t frames;                  /* frames the budget holds */
+    uint32_t frames_free;             /* frames attached to no group */
+    uint32_t slots_per_frame;         /* 8 */
+    uint32_t pad_;
+    uint64_t frame_bytes;             /* device bytes of one frame */
+    uint64_t edge_budget_bytes;       /* budget left to cache, staging and compaction */
+    uint64_t busy_slots;              /* bit s: slot s holds a query */
+} hytg_serve_info;
+hytg_status hytg_serve_get_info(hytg_ctx *ctx, hytg_serve_info *out);
 
 const char *hytg_status_str(hytg_status s);
 const char *hytg_last_error(hytg_ctx *ctx);
@@ -345,7 +418,9 @@ const char *hytg_last_error(hytg_ctx *ctx);
  * order them on one stream.  Errors: HYTG_ERR_ARG for a NULL pointer, an
  * unknown algorithm, V outside [1, 2^32 - 1], n_parts of 0 or above
  * HYTG_NOALLOC_MAX_PARTS, n_cached > n_parts or bad params; HYTG_ERR_CUDA if
- * the address lookup or a launch fails. */
+ * the address lookup or a launch fails, or if a CUDA error left by earlier
+ * work is already pending when the call starts (nothing is queued then, and
+ * that error is left pending for its owner to read). */
 #define HYTG_NOALLOC_MAX_PARTS 65536u
 
 typedef struct hytg_cost_params {

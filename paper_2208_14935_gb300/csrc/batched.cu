@@ -4,12 +4,12 @@
 // source), so each partition's edges cross the host link once per iteration
 // for all sources together.
 //
-// Per-vertex state, vertex-major so that one vertex's sources are contiguous:
+// Per-vertex state (values in frames of 8 sources, see BatchState):
 //   BFS/SSSP  fr[v], vis[v], nxt[v]  64-bit source masks (frontier, reached,
-//             reached or improved this iteration); val[v * 64 + s] level or
+//             reached or improved this iteration); *bval(v, s) level or
 //             distance of source s.
-//   PPR       delta[v * 32 + s], rank[v * 32 + s], msg[v * 32 + s] (the push
-//             of seed s taken this iteration), fr32[v] mask of seeds taken.
+//   PPR       *bdelta(v, s), *brank(v, s), *bmsg(v, s) (the push of seed s
+//             taken this iteration), fr32[v] mask of seeds taken.
 #include "common.cuh"
 #include "relax_tile.cuh"
 
@@ -19,22 +19,33 @@ namespace {
 
 inline unsigned int grid_for(unsigned long long n, unsigned int block) {
     unsigned long long g = (n + block - 1) / block;
-    if (g > 152ull * 32) g = 152ull * 32;
+    const unsigned long long cap = 32ull * device_sms();
+    if (g > cap) g = cap;
     return g == 0 ? 1u : (unsigned int)g;
 }
 
+__global__ void k_frame_init(BatchState b, unsigned long long V, unsigned int g) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long n = V * kFrameSources;
+    if (b.mode == kBatchPPR) {
+        for (unsigned long long i = t0; i < n; i += stride) {
+            b.delta[g][i] = 0.0f;
+            b.rank[g][i] = 0.0f;
+        }
+    } else {
+        for (unsigned long long i = t0; i < n; i += stride) b.val[g][i] = 0xFFFFFFFFu;
+    }
+}
+
+// Masks and bitmap of a new run (the frames are filled by k_frame_init).
 __global__ void k_b_init(BatchState b, unsigned long long V, unsigned long long n_words_alloc,
                          unsigned int *bm) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     if (b.mode == kBatchPPR) {
-        for (unsigned long long i = t0; i < V * 32; i += stride) {
-            b.delta[i] = 0.0f;
-            b.rank[i] = 0.0f;
-        }
         for (unsigned long long v = t0; v < V; v += stride) b.fr32[v] = 0;
     } else {
-        for (unsigned long long i = t0; i < V * 64; i += stride) b.val[i] = 0xFFFFFFFFu;
         for (unsigned long long v = t0; v < V; v += stride) {
             b.fr[v] = 0;
             b.vis[v] = 0;
@@ -51,11 +62,11 @@ __global__ void k_b_sources(BatchState b, const unsigned int *src, unsigned int 
     if (s >= K) return;
     const unsigned int v = src[s];
     if (b.mode == kBatchPPR) {
-        b.delta[(unsigned long long)v * 32 + s] = base;
+        *bdelta(b, v, s) = base;
     } else {
         atomicOr(&b.fr[v], 1ull << s);
         atomicOr(&b.vis[v], 1ull << s);
-        b.val[(unsigned long long)v * 64 + s] = 0u;
+        *bval(b, v, s) = 0u;
     }
     atomicOr(&bm[v >> 5], 1u << (v & 31));
 }
@@ -81,7 +92,7 @@ __global__ void k_b_commit(BatchState b, unsigned long long V, unsigned long lon
                 while (m) {
                     const int s = __ffsll((long long)m) - 1;
                     m &= m - 1;
-                    b.val[v * 64 + s] = level;
+                    *bval(b, v, (unsigned int)s) = level;
                 }
             }
             b.fr[v] = n;
@@ -117,16 +128,17 @@ __global__ void k_b_take(BatchState b, const unsigned long long *off, unsigned l
             bits &= bits - 1;
             const unsigned long long v = w * 32 + bit;
             const unsigned long long deg = off[v + 1] - off[v];
-            const unsigned long long i = v * 32 + lane;
-            float dl = b.delta[i];
-            const bool act = lane < (int)K && dl > eps;
+            // lanes are seeds; a seed past K, or in a frame not allocated, has no state
+            const bool has = lane < (int)K && b.delta[lane >> 3] != nullptr;
+            const float dl = has ? *bdelta(b, v, lane) : 0.0f;
+            const bool act = has && dl > eps;
             float msg = 0.0f;
             if (act) {
-                b.delta[i] = 0.0f;
-                b.rank[i] += dl;
+                *bdelta(b, v, lane) = 0.0f;
+                *brank(b, v, lane) += dl;
                 msg = deg ? damping * dl / (float)deg : 0.0f;
             }
-            b.msg[i] = msg;
+            if (has) *bmsg(b, v, lane) = msg;
             const unsigned int mask = __ballot_sync(0xffffffffu, act);
             if (lane == 0) b.fr32[v] = mask;
             if (mask) keep |= 1u << bit;
@@ -148,10 +160,10 @@ __global__ void k_serve_clear(BatchState b, unsigned long long V, unsigned int s
     for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
          v += stride) {
         if (b.mode == kBatchPPR) {
-            b.delta[v * 32 + slot] = 0.0f;
-            b.rank[v * 32 + slot] = 0.0f;
+            *bdelta(b, v, slot) = 0.0f;
+            *brank(b, v, slot) = 0.0f;
         } else {
-            b.val[v * 64 + slot] = 0xFFFFFFFFu;
+            *bval(b, v, slot) = 0xFFFFFFFFu;
             if (b.fr[v] & bit) b.fr[v] &= ~bit;
             if (b.vis[v] & bit) b.vis[v] &= ~bit;
             if (b.nxt[v] & bit) b.nxt[v] &= ~bit;
@@ -161,10 +173,10 @@ __global__ void k_serve_clear(BatchState b, unsigned long long V, unsigned int s
 __global__ void k_serve_seed(BatchState b, unsigned int slot, unsigned int src, float base,
                              unsigned int *bm) {
     if (b.mode == kBatchPPR) {
-        b.delta[(unsigned long long)src * 32 + slot] = base;
+        *bdelta(b, src, slot) = base;
         atomicOr(&bm[src >> 5], 1u << (src & 31));
     } else {
-        if (b.mode == kBatchSSSP) b.val[(unsigned long long)src * 64 + slot] = 0u;
+        if (b.mode == kBatchSSSP) *bval(b, src, slot) = 0u;
         atomicOr(&b.nxt[src], 1ull << slot);
     }
 }
@@ -180,9 +192,9 @@ __global__ void k_serve_extract(BatchState b, unsigned long long V, unsigned int
         const unsigned long long ov = perm ? perm[v] : v;
         if (b.mode == kBatchPPR) {
             const double S = sums[slot];
-            ((float *)out)[ov] = S > 0.0 ? (float)((double)b.rank[v * 32 + slot] / S) : 0.0f;
+            ((float *)out)[ov] = S > 0.0 ? (float)((double)*brank(b, v, slot) / S) : 0.0f;
         } else {
-            const unsigned int x = b.val[v * 64 + slot];
+            const unsigned int x = *bval(b, v, slot);
             ((unsigned int *)out)[ov] = (x == 0xFFFFFFFFu || b.mode != kBatchBFS) ? x : x - offset;
         }
     }
@@ -201,6 +213,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListA
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
         const int n = tile_setup<true>(sm, la, sum, t, tile, kb, ke, &k0);
+        if (t.link_ctr) count_link_reads<true>(sm, k0, n, 1u, t.link_ctr);
         unsigned int dv[kRelaxIPT];
         unsigned long long fv[kRelaxIPT];
 #pragma unroll
@@ -229,9 +242,14 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListA
     }
 }
 
-// Multi-source SSSP and batched PPR relax: one warp per edge, lanes are
-// sources (SSSP: s = lane and lane + 32; PPR: s = lane).  A warp loads 32
-// edges at once (coalesced) and then walks them with shuffles.
+// Multi-source SSSP and batched PPR relax.  A warp loads 32 edges at once
+// (coalesced), one per lane, each with its source vertex u and the mask of
+// sources active at u.  When those masks are dense (on average 8 or more
+// sources per edge) the warp walks its edges one at a time with a lane per
+// source (SSSP: s = lane and lane + 32; PPR: s = lane), reading each
+// source's value row in one sector per frame; otherwise every lane keeps its
+// own edge and loops over the sources active at its u, so that 32 edges'
+// loads are in flight together instead of one edge's.
 template <int MODE>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, ListArrays la,
                                                               const Summary *sum, RelaxTask t,
@@ -247,6 +265,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
         const int n = tile_setup<true>(sm, la, sum, t, tile, kb, ke, &k0);
+        if (t.link_ctr) count_link_reads<true>(sm, k0, n, MODE == kBatchSSSP ? 2u : 1u, t.link_ctr);
         const int per_warp = kTile / (kRelaxBlock / 32);           // 256 slots
         for (int c = wid * per_warp; c < (wid + 1) * per_warp && c < n; c += 32) {
             const int slot = c + lane;
@@ -264,6 +283,37 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                     atomicOr(la.err, 8u);
                 }
             }
+            if (dj == kInf) fj = 0;
+            unsigned int pop = __popcll(fj);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
+            if (pop < 8u * 32u) {
+                // sparse masks: a lane per edge, looping over its active sources
+                if (MODE == kBatchSSSP) {
+                    unsigned long long m = fj, imp = 0;
+                    while (m) {
+                        const unsigned int s = (unsigned int)(__ffsll((long long)m) - 1);
+                        m &= m - 1;
+                        const unsigned long long nd = (unsigned long long)__ldcg(bval(b, uj, s)) + wj;
+                        if (nd >= 0xFFFFFFFEull) {
+                            *overflow = 1u;
+                        } else if ((unsigned int)nd < __ldcg(bval(b, dj, s))) {
+                            atomicMin(bval(b, dj, s), (unsigned int)nd);
+                            imp |= 1ull << s;
+                        }
+                    }
+                    if (imp) atomicOr(&b.nxt[dj], imp);
+                } else {
+                    unsigned int m = (unsigned int)fj;
+                    if (m) atomicOr(&bm[dj >> 5], 1u << (dj & 31));
+                    while (m) {
+                        const unsigned int s = (unsigned int)(__ffs(m) - 1);
+                        m &= m - 1;
+                        atomicAdd(bdelta(b, dj, s), *bmsg(b, uj, s));
+                    }
+                }
+                continue;
+            }
             const int cnt = min(32, n - c);
             for (int jj = 0; jj < cnt; ++jj) {
                 const unsigned int v = __shfl_sync(0xffffffffu, dj, jj);
@@ -275,15 +325,14 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                     unsigned long long imp = 0;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int s = lane + 32 * h;
+                        const unsigned int s = lane + 32 * h;
                         bool better = false;
                         if ((f >> s) & 1ull) {
-                            const unsigned long long nd =
-                                (unsigned long long)__ldcg(&b.val[(unsigned long long)u * 64 + s]) + w;
+                            const unsigned long long nd = (unsigned long long)__ldcg(bval(b, u, s)) + w;
                             if (nd >= 0xFFFFFFFEull) {
                                 *overflow = 1u;
-                            } else if ((unsigned int)nd < __ldcg(&b.val[(unsigned long long)v * 64 + s])) {
-                                atomicMin(&b.val[(unsigned long long)v * 64 + s], (unsigned int)nd);
+                            } else if ((unsigned int)nd < __ldcg(bval(b, v, s))) {
+                                atomicMin(bval(b, v, s), (unsigned int)nd);
                                 better = true;
                             }
                         }
@@ -291,9 +340,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                     }
                     if (lane == 0 && imp) atomicOr(&b.nxt[v], imp);
                 } else {
-                    if ((f >> lane) & 1ull)
-                        atomicAdd(&b.delta[(unsigned long long)v * 32 + lane],
-                                  b.msg[(unsigned long long)u * 32 + lane]);
+                    if ((f >> lane) & 1ull) atomicAdd(bdelta(b, v, lane), *bmsg(b, u, lane));
                     if (lane == 0 && f) atomicOr(&bm[v >> 5], 1u << (v & 31));
                 }
             }
@@ -309,7 +356,7 @@ __global__ void k_b_out(BatchState b, unsigned long long V, unsigned int K, cons
          i += stride) {
         const unsigned long long s = i / V, v = i % V;
         const unsigned long long ov = perm ? perm[v] : v;
-        out[s * V + ov] = b.val[v * 64 + s];
+        out[s * V + ov] = *bval(b, v, (unsigned int)s);
     }
 }
 
@@ -317,12 +364,13 @@ __global__ void k_b_pr_sums(BatchState b, unsigned long long V, unsigned int K, 
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     double acc = 0.0, res = 0.0;
-    for (unsigned long long v = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; v < V;
-         v += nw) {
-        acc += b.rank[v * 32 + lane];
-        res += fabs((double)b.delta[v * 32 + lane]);
+    const bool has = lane < (int)K && b.rank[lane >> 3] != nullptr;
+    for (unsigned long long v = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+         has && v < V; v += nw) {
+        acc += *brank(b, v, lane);
+        res += fabs((double)*bdelta(b, v, lane));
     }
-    if (lane < (int)K) {
+    if (has) {
         atomicAdd(&sums[lane], acc);
         atomicAdd(&sums[32 + lane], res);
     }
@@ -336,7 +384,7 @@ __global__ void k_b_pr_out(BatchState b, unsigned long long V, unsigned int K, c
         const unsigned long long s = i / V, v = i % V;
         const unsigned long long ov = perm ? perm[v] : v;
         const double S = sums[s];
-        out[s * V + ov] = S > 0.0 ? (float)((double)b.rank[v * 32 + s] / S) : 0.0f;
+        out[s * V + ov] = S > 0.0 ? (float)((double)*brank(b, v, (unsigned int)s) / S) : 0.0f;
     }
 }
 
@@ -345,8 +393,16 @@ __global__ void k_b_pr_out(BatchState b, unsigned long long V, unsigned int K, c
 cudaError_t launch_b_init(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
                           const unsigned int *src_dev, unsigned int K, float base, unsigned int *bm,
                           cudaStream_t s) {
-    k_b_init<<<grid_for(V * (b.mode == kBatchPPR ? 32 : 64), 256), 256, 0, s>>>(b, V, n_words_alloc, bm);
-    k_b_sources<<<1, 64, 0, s>>>(b, src_dev, K, base, bm);
+    k_b_init<<<grid_for(V, 256), 256, 0, s>>>(b, V, n_words_alloc, bm);
+    if (K) k_b_sources<<<1, 64, 0, s>>>(b, src_dev, K, base, bm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_init(const BatchState &b, unsigned long long V, unsigned int g, cudaStream_t s) {
+    const bool ok = b.mode == kBatchPPR ? (g < kMaxPprFrames && b.delta[g] && b.rank[g])
+                                        : (g < kMaxFrames && b.val[g]);
+    if (!ok) return cudaErrorInvalidValue;
+    k_frame_init<<<grid_for(V * kFrameSources, 256), 256, 0, s>>>(b, V, g);
     return cudaGetLastError();
 }
 

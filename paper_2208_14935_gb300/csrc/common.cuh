@@ -117,6 +117,10 @@ __host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long 
 }
 
 // ------------------------------------------------------------- launchers
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount),
+// read once per device and cached; grid caps are multiples of it.
+unsigned int device_sms();
+
 struct GraphDev {
     const unsigned long long *off;      // V+1 row offsets (device)
     unsigned long long V, n_words_alloc;
@@ -170,15 +174,37 @@ struct AlgoState {
 
 enum BatchMode : int { kBatchNone = 0, kBatchBFS = 1, kBatchSSSP = 2, kBatchPPR = 3 };
 
+// Per-source state of batched runs and serving lives in frames of
+// kFrameSources consecutive sources, so that serving can allocate and release
+// it eight queries at a time.  Frame g holds sources [8 g, 8 g + 8): BFS/SSSP
+// val[g][v * 8 + (s & 7)] (V * 32 bytes); PPR delta[g], rank[g], msg[g], each
+// V * 8 floats (V * 96 bytes in all).  A warp that reads every source of one
+// vertex reads one 32-byte sector per frame, as a contiguous vertex-major
+// layout would.  Only frames of sources that can be active are read.
+constexpr unsigned int kFrameSources = 8;
+constexpr unsigned int kMaxFrames = 8;           // 64 BFS/SSSP sources; PPR uses 4 (32 seeds)
+constexpr unsigned int kMaxPprFrames = 4;
 struct BatchState {
     int mode;
     unsigned long long *fr, *vis, *nxt;   // BFS/SSSP source masks
-    unsigned int *val;                    // BFS level / SSSP distance, [v * 64 + s]
-    float *delta, *rank, *msg;            // PPR, [v * 32 + s]
+    unsigned int *val[kMaxFrames];        // BFS level / SSSP distance frames (nullptr: none)
+    float *delta[kMaxPprFrames], *rank[kMaxPprFrames], *msg[kMaxPprFrames];   // PPR frames
     unsigned int *fr32;                   // PPR seeds taken at v this iteration
     unsigned long long *alive;            // OR of every vertex's frontier mask (serving)
     const LoopCtl *loop;                  // device loop: level from loop->it; relax gated by loop->work
 };
+__device__ __forceinline__ unsigned int *bval(const BatchState &b, unsigned long long v, unsigned int s) {
+    return b.val[s >> 3] + v * kFrameSources + (s & 7);
+}
+__device__ __forceinline__ float *bdelta(const BatchState &b, unsigned long long v, unsigned int s) {
+    return b.delta[s >> 3] + v * kFrameSources + (s & 7);
+}
+__device__ __forceinline__ float *brank(const BatchState &b, unsigned long long v, unsigned int s) {
+    return b.rank[s >> 3] + v * kFrameSources + (s & 7);
+}
+__device__ __forceinline__ float *bmsg(const BatchState &b, unsigned long long v, unsigned int s) {
+    return b.msg[s >> 3] + v * kFrameSources + (s & 7);
+}
 constexpr unsigned int kHubReplicas = 256;
 
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
@@ -201,6 +227,8 @@ struct RelaxTask {
     unsigned long long first_entry;     // route-relative entry holding k_begin
     bool device_sized;                  // take k_end from the summary (k_begin = 0)
     unsigned long long src_len;         // valid indices of dst / w: [0, src_len)
+    unsigned long long *link_ctr;       // host-memory reads (Z relax, C gather): {32-byte
+                                        // sectors, 128-byte lines} read, or nullptr
 };
 
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
@@ -208,10 +236,21 @@ cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summar
 // Both tasks device-sized (routes of the current list); plain runs only.
 cudaError_t launch_relax_pair(const AlgoState &st, const ListArrays &la, const Summary *sum,
                               const RelaxTask &ta, const RelaxTask &tb, int grid, cudaStream_t s);
+// Second pass (Sec. VI-A) over vertices [vlo, vhi) (vlo a multiple of 32)
+// whose edges [E0, E1) are resident in dst / w (CSR edge shift at index 0):
+// a take launch and an edge-balanced push launch.  Scratch shared by every
+// second pass of a run (their vertex and edge ranges never overlap):
+constexpr unsigned long long kSpChunk = 256;      // edges per push chunk
+struct SecondPassScratch {
+    unsigned int *owner;    // per CSR chunk of kSpChunk edges: vertex owning its first edge
+    unsigned int *pay;      // per vertex: value it pushes (taken vertices)
+    unsigned int *mask;     // per 32 vertices: bit set when taken
+};
 cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *off,
                                const unsigned int *dst, const unsigned int *w, long long shift,
                                unsigned long long src_len, unsigned long long vlo,
-                               unsigned long long vhi, unsigned long long *edges_out,
+                               unsigned long long vhi, unsigned long long E0, unsigned long long E1,
+                               const SecondPassScratch &sc, unsigned long long *edges_out,
                                unsigned int *err, cudaStream_t s);
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
@@ -220,6 +259,9 @@ cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxT
 cudaError_t launch_b_init(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
                           const unsigned int *src_dev, unsigned int K, float base, unsigned int *bm,
                           cudaStream_t s);
+// Fill frame g of the batched state with "no value" (BFS/SSSP: unreached;
+// PPR: zero delta and rank), as every frame must hold before it is used.
+cudaError_t launch_frame_init(const BatchState &b, unsigned long long V, unsigned int g, cudaStream_t s);
 cudaError_t launch_b_commit(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
                             unsigned int level, unsigned int *bm, cudaStream_t s);
 cudaError_t launch_b_take(const BatchState &b, const unsigned long long *off,
@@ -256,7 +298,7 @@ cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *
                                  unsigned long long V, unsigned long long n_words_alloc,
                                  cudaStream_t s);
 cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, int skew, bool gen,
-                             cudaStream_t s);
+                             cudaStream_t s, float *rep = nullptr, unsigned int n_rep = 0);
 cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
                             int grid, cudaStream_t s);
 

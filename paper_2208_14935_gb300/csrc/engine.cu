@@ -37,12 +37,21 @@ using namespace hytg;
 
 namespace {
 
-constexpr int kMaxStreams = 8;
-constexpr int kKindSecondPass = 12;     // timed kind beyond HYTG_K_*: hytg_stats.second_pass_ms
+constexpr int kMaxStreams = 8;        // F compute streams
+constexpr int kMaxSlots = 16;         // staging slots, each with its own copy stream
+constexpr uint64_t kPoolSlack = 16384;  // budget pool bytes beyond the budget: alignment padding
+constexpr int kKindSecondPass = HYTG_K_SECOND_PASS;   // timed kind beyond the first 12: second_pass_ms
+// Second-pass edge counters of one run: slot 0 for the passes inside the
+// device-loop graph, slots 1.. for host-issued launches in issue order; the
+// last slot is shared by every launch beyond it.
+constexpr uint32_t kSpSlots = 16384;
 
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;
+    int stream;                 // 0 main, 1 compaction, 2 + i F stream i
+    uint64_t bytes, edges, vertices;
+    int sp_slot;                // second pass: its counter slot, else -1
 };
 
 // One F task after combination: partitions [i, j], their edges, and the
@@ -114,9 +123,10 @@ struct Carve {
     uint32_t n_cached = 0;
     uint64_t cache_edges = 0;
     uint32_t *cache_dst = nullptr, *cache_w = nullptr;
-    uint32_t *slot_dst[kMaxStreams] = {}, *slot_w[kMaxStreams] = {};
+    uint32_t *slot_dst[kMaxSlots] = {}, *slot_w[kMaxSlots] = {};
     uint32_t *cmp_dst = nullptr, *cmp_w = nullptr;
     uint64_t used = 0;
+    uint64_t end = 0;           // bytes of the pool the carve spans (with alignment padding)
 };
 
 }  // namespace
@@ -127,11 +137,14 @@ struct hytg_ctx {
 
     cudaStream_t s_main = nullptr, s_c = nullptr;
     cudaStream_t s_f[kMaxStreams] = {};
+    cudaStream_t s_cp[kMaxSlots] = {};                   // copy stream of each staging slot
     cudaEvent_t ev_sum[2] = {}, ev_bin = nullptr, ev_f[kMaxStreams] = {}, ev_c = nullptr;
+    cudaEvent_t ev_copied[kMaxSlots] = {}, ev_free[kMaxSlots] = {};   // slot filled / slot's last use done
     cudaEvent_t ev_run[2] = {};                          // device time of a run
 
     // graph
     bool loaded = false;
+    int symmetric = -1;                                  // CSR symmetry: -1 not checked yet, 0 no, 1 yes
     uint64_t V = 0, E = 0;
     bool weighted = false;
     uint32_t *h_dst = nullptr, *h_w = nullptr;          // pinned, mapped
@@ -148,22 +161,36 @@ struct hytg_ctx {
     // batched runs (several sources in one run, sharing every transfer)
     BatchState bs{};
     bool bs_alloc_mask = false, bs_alloc_ppr = false;
+    unsigned int *own_val[kMaxFrames] = {};              // hytg_run's BFS/SSSP frames (V * 32 B each)
+    float *own_ppr[kMaxPprFrames] = {};                  // hytg_run's PPR frames (V * 96 B each)
     int batch_mode = kBatchNone;
     unsigned int batch_K = 0;
     unsigned int *d_src = nullptr;                       // 64 source ids
     unsigned long long *d_pay64 = nullptr;
     unsigned int *d_vid = nullptr;
     void *d_bout = nullptr;                              // K x V results
+    uint32_t bout_rows = 0;                              // rows of V results d_bout holds
     unsigned long long *d_src_work = nullptr;
     double *d_bsums = nullptr;
     unsigned long long *d_alive = nullptr;
-    unsigned long long *d_extra = nullptr;               // second-pass edge counter
+    unsigned long long *d_sp = nullptr;                  // second-pass edge counters (kSpSlots)
+    unsigned int *d_sp_owner = nullptr;                  // second pass: owner of each kSpChunk-edge chunk
+    unsigned int *d_sp_mask = nullptr;                   // second pass: taken bits (one word per 32 vertices)
+    uint32_t sp_launches = 0;                            // host-issued second passes this run
+    unsigned long long *d_link_ctr = nullptr;            // per route {sectors, lines} read from host memory
     // serving (continuous batching over the batched state)
     bool serving = false;
     int serve_algo = -1;
     uint32_t serve_it = 0;
     uint64_t serve_busy = 0, serve_alive = 0;
     uint32_t serve_admit_it[64] = {};
+    // serving's query frames, carved from the budget pool behind the edge-side carve
+    char *serve_frame_base = nullptr;
+    uint64_t serve_frame_bytes = 0;
+    uint32_t serve_frames = 0;                           // frames the budget holds
+    uint32_t serve_frames_used = 0;                      // bit f: frame f attached to a group
+    int serve_group_frame[kMaxFrames] = {};              // frame of each group of 8 slots, or -1
+    uint64_t serve_edge_budget = 0;
 
     // partitions
     uint64_t part_edges = 0, max_part_edges = 0;
@@ -204,6 +231,7 @@ struct hytg_ctx {
     double alpha = 0.8, beta = 0.4, gamma = 0.625, m = 128, MR = 256, k = 4;
     double part_bytes = 4.0 * 1024 * 1024;
     double streams = 4, staging_frac = 0.5, compact_frac = 0.05;
+    double prefetch_slots = 2;                           // staging slots beyond one per F stream
     double force_route = -1, seed = 1, pr_damping = 0.85, pr_eps = 1e-9, max_iters = 1e8;
     double timing = 0;
     double hub_frac = 0.08;                              // Sec. VI-A: top 8 % of vertices
@@ -213,6 +241,7 @@ struct hytg_ctx {
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
+    double serve_frames_param = 0;                       // serving: cap on query frames (0: what the slots need)
     uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
@@ -221,6 +250,7 @@ struct hytg_ctx {
     hytg_stats stats{};
     std::vector<hytg_iter_record> iters;
     std::vector<TimedLaunch> timed;
+    std::vector<hytg_timed_launch> timeline;             // the last run's timed launches
     std::vector<FTask> f_tasks_buf;
     std::vector<std::pair<size_t, cudaEvent_t>> iter_ev; // (iteration index, start mark), timing on
     std::vector<cudaEvent_t> ev_pool;
@@ -291,10 +321,14 @@ void free_graph(hytg_ctx *c) {
     dfree(c->d_out); dfree(c->d_ebase); dfree(c->d_soff); dfree(c->d_pay); dfree(c->d_tiles);
     dfree(c->d_part_wb); dfree(c->d_part_eb); dfree(c->d_sumbuf); dfree(c->d_perm); dfree(c->d_round_part);
     dfree(c->d_hub_rep);
+    dfree(c->d_sp_owner);
+    dfree(c->d_sp_mask);
     c->n_hub_rep = 0;
-    dfree(c->bs.fr); dfree(c->bs.vis); dfree(c->bs.nxt); dfree(c->bs.val);
-    dfree(c->bs.delta); dfree(c->bs.rank); dfree(c->bs.msg); dfree(c->bs.fr32);
+    dfree(c->bs.fr); dfree(c->bs.vis); dfree(c->bs.nxt); dfree(c->bs.fr32);
     dfree(c->d_pay64); dfree(c->d_vid); dfree(c->d_bout);
+    c->bout_rows = 0;
+    for (auto &f : c->own_val) dfree(f);
+    for (auto &f : c->own_ppr) dfree(f);
     c->bs = BatchState{};
     c->bs_alloc_mask = c->bs_alloc_ppr = false;
     c->batch_mode = kBatchNone;
@@ -307,6 +341,7 @@ void free_graph(hytg_ctx *c) {
         c->h_sumbuf[i] = nullptr;
     }
     c->loaded = false;
+    c->symmetric = -1;
     c->have_result = false;
     c->h_off.clear();
     c->cache_filled_arrays = 0;
@@ -321,6 +356,64 @@ void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &
     for (unsigned t = 1; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
     fn(0, n / nt);
     for (auto &x : th) x.join();
+}
+
+// fn(v_lo, v_hi) over vertex ranges holding about equal numbers of edges
+// (hub sorting puts most edges in the first few vertices).
+void parallel_edge_balanced(const std::vector<uint64_t> &off, uint64_t V,
+                            const std::function<void(uint64_t, uint64_t)> &fn) {
+    const uint64_t E = off[V];
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (E < (1u << 20)) nt = 1;
+    std::vector<uint64_t> vb(nt + 1, V);
+    vb[0] = 0;
+    for (unsigned t = 1; t < nt; ++t)
+        vb[t] = (uint64_t)(std::lower_bound(off.begin(), off.begin() + V + 1, E * t / nt) - off.begin());
+    for (unsigned t = 1; t <= nt; ++t) vb[t] = std::max(vb[t], vb[t - 1]);
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(fn, vb[t], vb[t + 1]);
+    fn(vb[0], vb[1]);
+    for (auto &x : th) x.join();
+}
+
+// Whether the loaded CSR is symmetric, as connected components need (the
+// weakly connected components of a directed graph are those of its
+// symmetrised form, Sec. VII-A runs CC on directed graphs): every edge u->v
+// has a reverse v->u with the same multiplicity, a self-loop being its own
+// reverse.  In-degrees must equal out-degrees; the reverse rows then have the
+// CSR's own offsets, and each row, sorted, must equal the sorted list of the
+// vertex's in-neighbours.  O(E) plus the row sorts, on host threads.
+bool csr_symmetric(const std::vector<uint64_t> &off, const uint32_t *dst, uint64_t V) {
+    const uint64_t E = off[V];
+    std::vector<uint64_t> indeg(V, 0);
+    parallel_chunks(E, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t e = lo; e < hi; ++e) __atomic_fetch_add(&indeg[dst[e]], 1ull, __ATOMIC_RELAXED);
+    });
+    std::atomic<bool> ok{true};
+    parallel_chunks(V, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t v = lo; v < hi; ++v)
+            if (indeg[v] != off[v + 1] - off[v]) { ok = false; return; }
+    });
+    if (!ok) return false;
+    std::vector<uint64_t> cur(off.begin(), off.begin() + V);
+    std::vector<uint32_t> rev(std::max<uint64_t>(E, 1));
+    parallel_edge_balanced(off, V, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t u = lo; u < hi; ++u)
+            for (uint64_t e = off[u]; e < off[u + 1]; ++e)
+                rev[__atomic_fetch_add(&cur[dst[e]], 1ull, __ATOMIC_RELAXED)] = (uint32_t)u;
+    });
+    parallel_edge_balanced(off, V, [&](uint64_t lo, uint64_t hi) {
+        std::vector<uint32_t> row;
+        for (uint64_t v = lo; v < hi && ok; ++v) {
+            const uint64_t b = off[v], n = off[v + 1] - b;
+            if (n == 0) continue;
+            row.assign(dst + b, dst + b + n);
+            std::sort(row.begin(), row.end());
+            std::sort(rev.begin() + b, rev.begin() + b + n);
+            if (!std::equal(row.begin(), row.end(), rev.begin() + b)) ok = false;
+        }
+    });
+    return ok;
 }
 
 // Layout of the summary buffer: the Summary, then the per-partition arrays.
@@ -439,31 +532,34 @@ hytg_status upload_partitions(hytg_ctx *c) {
     return HYTG_OK;
 }
 
-// Split the budget into staging slots (F), the compaction buffer (C) and the
-// resident cache (the rest, whole partitions from id 0 upwards).
-hytg_status plan_carve(hytg_ctx *c, int n_arrays) {
+// Split the budget (or `edge_budget` bytes of it, when serving keeps the
+// rest for query frames) into staging slots (F), the compaction buffer (C)
+// and the resident cache (the rest, whole partitions from id 0 upwards).
+hytg_status plan_carve(hytg_ctx *c, int n_arrays, uint64_t edge_budget = 0) {
+    const uint64_t B = edge_budget ? edge_budget : c->budget;
     Carve &cv = c->carve;
     const uint64_t pe = c->part_edges;
     Carve n;
     n.n_arrays = n_arrays;
-    n.budget = c->budget;
+    n.budget = B;
     n.part_edges = pe;
     const uint64_t eb = 4ull * n_arrays;
     const uint64_t min_slot = std::max<uint64_t>(c->max_part_edges, 1);
     const uint64_t compact_min = std::max<uint64_t>(kTile, 1);
-    if (c->budget < (min_slot + compact_min) * eb)
-        return fail(c, HYTG_ERR_BUDGET, "device budget " + std::to_string(c->budget) +
+    if (B < (min_slot + compact_min) * eb)
+        return fail(c, HYTG_ERR_BUDGET, "device budget " + std::to_string(B) +
                                             " B is below one staging slot of the largest partition (" +
                                             std::to_string(min_slot * eb) + " B) plus the minimum compaction buffer (" +
                                             std::to_string(compact_min * eb) + " B)");
-    uint64_t stage_cap = std::max<uint64_t>((uint64_t)(c->budget * c->staging_frac), min_slot * eb);
-    stage_cap = std::min<uint64_t>(stage_cap, c->budget - compact_min * eb);
+    uint64_t stage_cap = std::max<uint64_t>((uint64_t)(B * c->staging_frac), min_slot * eb);
+    stage_cap = std::min<uint64_t>(stage_cap, B - compact_min * eb);
     uint64_t slot_edges = std::max<uint64_t>((uint64_t)c->k * pe, min_slot);
     if (slot_edges * eb > stage_cap) slot_edges = std::max<uint64_t>(min_slot, stage_cap / eb);
     uint64_t n_slots = stage_cap / (slot_edges * eb);
-    n_slots = std::max<uint64_t>(1, std::min<uint64_t>(n_slots, (uint64_t)c->streams));
-    uint64_t rem = c->budget - n_slots * slot_edges * eb;
-    uint64_t compact_edges = std::max<uint64_t>(compact_min, (uint64_t)(c->budget * c->compact_frac) / eb);
+    n_slots = std::max<uint64_t>(1, std::min<uint64_t>({n_slots, (uint64_t)(c->streams + c->prefetch_slots),
+                                                        (uint64_t)kMaxSlots}));
+    uint64_t rem = B - n_slots * slot_edges * eb;
+    uint64_t compact_edges = std::max<uint64_t>(compact_min, (uint64_t)(B * c->compact_frac) / eb);
     compact_edges = std::min<uint64_t>(compact_edges, rem / eb);
     compact_edges = compact_edges / kTile * kTile;
     if (compact_edges < (uint64_t)kTile) compact_edges = kTile;
@@ -489,9 +585,10 @@ hytg_status plan_carve(hytg_ctx *c, int n_arrays) {
     }
     n.cmp_dst = (uint32_t *)(base + o); o = align(o + compact_edges * 4);
     if (n_arrays == 2) { n.cmp_w = (uint32_t *)(base + o); o = align(o + compact_edges * 4); }
-    // at most 20 pieces, each padded by < 256 B: the pool holds budget + 8 KiB
-    if (o > c->budget + 8192)
+    // at most 36 pieces, each padded by < 256 B: the pool holds budget + kPoolSlack
+    if (o > B + kPoolSlack)
         return fail(c, HYTG_ERR_BUDGET, "internal: budget carve exceeds the pool");
+    n.end = o;
     n.used = n.cache_edges * eb + n.n_slots * slot_edges * eb + compact_edges * eb;
     if (c->cache_filled_arrays != n_arrays || c->carve.cache_dst != n.cache_dst ||
         c->cache_filled_n != n.n_cached)
@@ -509,11 +606,24 @@ cudaEvent_t pool_event(hytg_ctx *c) {
     return c->ev_pool[c->ev_used++];
 }
 
+int stream_index(const hytg_ctx *c, cudaStream_t s) {
+    if (s == c->s_c) return 1;
+    for (int i = 0; i < kMaxStreams; ++i)
+        if (s == c->s_f[i]) return 2 + i;
+    for (int i = 0; i < kMaxSlots; ++i)
+        if (s == c->s_cp[i]) return 2 + kMaxStreams + i;
+    return 0;
+}
+
+// CUDA-event interval of one launch (timing on); bytes, edges, vertices and
+// the second-pass counter slot are filled in by the caller when they apply.
 struct ScopedTime {
     hytg_ctx *c;
     int kind;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
+    uint64_t bytes = 0, edges = 0, vertices = 0;
+    int sp_slot = -1;
     ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_, bool kernel = true) : c(c_), kind(kind_), s(s_) {
         const unsigned k = (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
         if (c->capturing) {              // inside a graph body: counted per body run
@@ -530,10 +640,23 @@ struct ScopedTime {
         if (a) {
             cudaEvent_t b = pool_event(c);
             cudaEventRecord(b, s);
-            c->timed.push_back({kind, a, b});
+            c->timed.push_back({kind, a, b, stream_index(c, s), bytes, edges, vertices, sp_slot});
         }
     }
 };
+
+// A second pass is two launches (take, push); ScopedTime counted the first.
+void count_second_launch(hytg_ctx *c) {
+    if (c->capturing) c->loop_kernels += 1;
+    else c->stats.kernel_launches += 1;
+}
+
+// Counter slot of the next host-issued second pass.
+unsigned long long *next_sp_slot(hytg_ctx *c, int *slot) {
+    const uint32_t k = std::min<uint32_t>(++c->sp_launches, kSpSlots - 1);
+    *slot = (int)k;
+    return c->d_sp + k;
+}
 
 GraphDev graph_dev(hytg_ctx *c) {
     GraphDev g;
@@ -545,6 +668,16 @@ GraphDev graph_dev(hytg_ctx *c) {
     g.round_part = c->d_round_part;
     g.N = (unsigned int)(c->part_vb.size() - 1);
     return g;
+}
+
+// The second passes' scratch; their push values live in d_out, which holds
+// nothing until the run's finalisation writes the result.
+SecondPassScratch sp_scratch(hytg_ctx *c) {
+    SecondPassScratch sc;
+    sc.owner = c->d_sp_owner;
+    sc.pay = (unsigned int *)c->d_out;
+    sc.mask = c->d_sp_mask;
+    return sc;
 }
 
 ListArrays list_arrays(hytg_ctx *c) {
@@ -627,19 +760,24 @@ cudaError_t relax_any(hytg_ctx *c, const AlgoState &st, const ListArrays &la, co
     return launch_relax(st, la, sum, t, cap, s);
 }
 
-// Device arrays of batched runs, allocated on first use and kept with the graph.
-hytg_status ensure_batch(hytg_ctx *c, int mode) {
+// Device arrays of batched runs and serving that do not grow with the
+// number of sources (masks, list payloads, result rows), allocated on first
+// use and kept with the graph (vertex-side data, outside the budget).  Every
+// frame pointer is cleared; attach_own_frames or the serving calls set them.
+hytg_status ensure_batch(hytg_ctx *c, int mode, uint32_t out_rows) {
     const uint64_t V = c->V;
     if (!c->d_pay64) {
         CK(cudaMalloc(&c->d_pay64, V * 8));
         CK(cudaMalloc(&c->d_vid, V * 4));
-        CK(cudaMalloc(&c->d_bout, V * 64 * 4));
+    }
+    if (c->bout_rows < out_rows) {
+        dfree(c->d_bout);
+        c->bout_rows = 0;
+        CK(cudaMalloc(&c->d_bout, V * 4 * out_rows));
+        c->bout_rows = out_rows;
     }
     if (mode == kBatchPPR) {
         if (!c->bs_alloc_ppr) {
-            CK(cudaMalloc(&c->bs.delta, V * 32 * 4));
-            CK(cudaMalloc(&c->bs.rank, V * 32 * 4));
-            CK(cudaMalloc(&c->bs.msg, V * 32 * 4));
             CK(cudaMalloc(&c->bs.fr32, V * 4));
             c->bs_alloc_ppr = true;
         }
@@ -647,11 +785,51 @@ hytg_status ensure_batch(hytg_ctx *c, int mode) {
         CK(cudaMalloc(&c->bs.fr, V * 8));
         CK(cudaMalloc(&c->bs.vis, V * 8));
         CK(cudaMalloc(&c->bs.nxt, V * 8));
-        CK(cudaMalloc(&c->bs.val, V * 64 * 4));
         c->bs_alloc_mask = true;
     }
     c->bs.mode = mode;
     c->bs.alive = c->d_alive;
+    for (auto &p : c->bs.val) p = nullptr;
+    for (uint32_t g = 0; g < kMaxPprFrames; ++g) c->bs.delta[g] = c->bs.rank[g] = c->bs.msg[g] = nullptr;
+    return HYTG_OK;
+}
+
+// Bytes of one frame of 8 sources: BFS/SSSP values, or PPR delta, rank, msg.
+uint64_t frame_bytes(const hytg_ctx *c, int mode) {
+    const uint64_t b = c->V * kFrameSources * 4ull * (mode == kBatchPPR ? 3 : 1);
+    return (b + 255) & ~uint64_t(255);
+}
+
+// Point group g's frame at `mem` (nullptr: the group has no frame).
+void set_group_frame(hytg_ctx *c, uint32_t g, char *mem) {
+    const uint64_t blk = c->V * kFrameSources * 4ull;
+    if (c->bs.mode == kBatchPPR) {
+        c->bs.delta[g] = mem ? (float *)mem : nullptr;
+        c->bs.rank[g] = mem ? (float *)(mem + blk) : nullptr;
+        c->bs.msg[g] = mem ? (float *)(mem + 2 * blk) : nullptr;
+    } else {
+        c->bs.val[g] = mem ? (unsigned int *)mem : nullptr;
+    }
+}
+
+// Serving: give group g's frame back once none of its slots holds a query.
+void release_idle_frame(hytg_ctx *c, uint32_t g) {
+    if (g >= kMaxFrames || c->serve_group_frame[g] < 0) return;
+    if ((c->serve_busy >> (g * kFrameSources)) & 0xFFull) return;
+    c->serve_frames_used &= ~(1u << c->serve_group_frame[g]);
+    c->serve_group_frame[g] = -1;
+    set_group_frame(c, g, nullptr);
+}
+
+// Frames of a batched hytg_run: one per 8 sources, owned by the context
+// (outside the budget, like every batched run's per-source state).
+hytg_status attach_own_frames(hytg_ctx *c, int mode, uint32_t K) {
+    const uint32_t groups = (K + kFrameSources - 1) / kFrameSources;
+    for (uint32_t g = 0; g < groups; ++g) {
+        void **own = mode == kBatchPPR ? (void **)&c->own_ppr[g] : (void **)&c->own_val[g];
+        if (!*own) CK(cudaMalloc(own, frame_bytes(c, mode)));
+        set_group_frame(c, g, (char *)*own);
+    }
     return HYTG_OK;
 }
 
@@ -717,14 +895,14 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
     Summary *sum = (Summary *)c->d_sumbuf;
     { ScopedTime t(c, HYTG_K_BIN, s); CK(launch_bin(g, st, pa, la, sum, s)); }
     if (!c->capturing) CK(cudaEventRecord(c->ev_bin, s));
-    const int cap = 152 * 4;
+    const int cap = 4 * (int)device_sms();
     if (c->capturing && c->batch_mode == kBatchNone && c->carve.n_cached > 0) {
         // device loop body: cache and zero-copy routes in one launch
         RelaxTask tc{}, tz{};
         tc.route = kRouteCache; tc.mode = kModeDevice; tc.dst = c->carve.cache_dst; tc.w = c->carve.cache_w;
         tc.shift = 0; tc.device_sized = true; tc.src_len = c->carve.cache_edges;
         tz.route = kRouteZ; tz.mode = kModeHost; tz.dst = c->m_dst; tz.w = c->m_w; tz.shift = 0;
-        tz.device_sized = true; tz.src_len = c->E;
+        tz.device_sized = true; tz.src_len = c->E; tz.link_ctr = c->d_link_ctr + 2 * kRouteZ;
         {
             ScopedTime tm(c, HYTG_K_RELAX_Z, s);
             CK(launch_relax_pair(st, la, sum, tc, tz, cap, s));
@@ -732,8 +910,9 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
         if (cache_second_pass_on(c, algo)) {
             ScopedTime tm(c, kKindSecondPass, s);
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
-                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
-                                  c->d_err, s));
+                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], 0,
+                                  c->part_eb[c->carve.n_cached], sp_scratch(c), c->d_sp, c->d_err, s));
+            count_second_launch(c);
         }
         return HYTG_OK;
     }
@@ -747,16 +926,19 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
         }
         if (cache_second_pass_on(c, algo)) {
             ScopedTime tm(c, kKindSecondPass, s);
+            unsigned long long *ctr = next_sp_slot(c, &tm.sp_slot);
+            tm.vertices = c->part_vb[c->carve.n_cached];
             CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
-                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], c->d_extra,
-                                  c->d_err, s));
+                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], 0,
+                                  c->part_eb[c->carve.n_cached], sp_scratch(c), ctr, c->d_err, s));
+            count_second_launch(c);
             c->stats.second_pass_vertices += c->part_vb[c->carve.n_cached];
         }
     }
     {
         RelaxTask t{};
         t.route = kRouteZ; t.mode = kModeHost; t.dst = c->m_dst; t.w = c->m_w; t.shift = 0;
-        t.device_sized = true; t.src_len = c->E;
+        t.device_sized = true; t.src_len = c->E; t.link_ctr = c->d_link_ctr + 2 * kRouteZ;
         ScopedTime tm(c, HYTG_K_RELAX_Z, s);
         CK(relax_any(c, st, la, sum, t, cap, s));
     }
@@ -948,6 +1130,7 @@ hytg_status host_compact(hytg_ctx *c, int algo, unsigned int bucket, const Summa
         if (bad) return fail(c, HYTG_ERR_CUDA, "host compaction: active list out of range");
         {
             ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c, false);
+            tm.bytes = (ce - cb) * 4ull * n_arrays;
             CK(cudaMemcpyAsync(cv.cmp_dst, sd, (ce - cb) * 4, cudaMemcpyHostToDevice, c->s_c));
             if (n_arrays == 2)
                 CK(cudaMemcpyAsync(cv.cmp_w, sw, (ce - cb) * 4, cudaMemcpyHostToDevice, c->s_c));
@@ -960,7 +1143,7 @@ hytg_status host_compact(hytg_ctx *c, int algo, unsigned int bucket, const Summa
         r.src_len = ce - cb;
         {
             ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
-            CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
+            CK(relax_any(c, st, la, dsum, r, 8 * (int)device_sms(), c->s_c));
         }
     }
     c->stats.host_compact_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1018,24 +1201,34 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     uint64_t f_bytes = 0;
     uint32_t n_tasks = 0;
     f_streams_used.clear();
+    // Tasks take the staging slots in turn and the F compute streams in turn;
+    // there are more slots than compute streams, and each slot has its own
+    // copy stream, so the copy of a later task runs while earlier tasks'
+    // relaxes and second passes still hold their slots.
+    const uint32_t n_fs = std::max<uint32_t>(1, std::min<uint32_t>(cv.n_slots, (uint32_t)c->streams));
     for (const FTask &ft : tasks) {
         const uint32_t i0 = ft.i, j = ft.j;
         const uint64_t edges = ft.edges;
         const uint32_t slot = n_tasks % cv.n_slots;
-        cudaStream_t fs = c->s_f[slot];
+        const uint32_t fi = n_tasks % n_fs;
+        cudaStream_t fs = c->s_f[fi], cs = c->s_cp[slot];
         const uint64_t e0 = c->part_eb[i0];
         {
             // the copy needs only the route decision (already on the host)
-            // and the slot's previous relax (same stream), not the lists
-            ScopedTime t(c, HYTG_K_COPY_F, fs);
-            CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+            // and the end of the slot's previous use, not the lists
+            CK(cudaStreamWaitEvent(cs, c->ev_free[slot], 0));
+            ScopedTime t(c, HYTG_K_COPY_F, cs);
+            t.bytes = edges * ebytes;
+            CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, cs));
             if (n_arrays == 2)
-                CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, fs));
+                CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, cs));
         }
-        if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)slot) == f_streams_used.end()) {
-            f_streams_used.push_back((int)slot);
+        CK(cudaEventRecord(c->ev_copied[slot], cs));
+        if (std::find(f_streams_used.begin(), f_streams_used.end(), (int)fi) == f_streams_used.end()) {
+            f_streams_used.push_back((int)fi);
             CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
         }
+        CK(cudaStreamWaitEvent(fs, c->ev_copied[slot], 0));
         RelaxTask t{};
         t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
         t.shift = (long long)e0;
@@ -1046,14 +1239,20 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         t.src_len = edges;
         {
             ScopedTime tm(c, HYTG_K_RELAX_F, fs);
-            CK(relax_any(c, st, la, dsum, t, 152 * 8, fs));
+            tm.edges = t.k_end - t.k_begin;
+            CK(relax_any(c, st, la, dsum, t, 8 * (int)device_sms(), fs));
         }
         if (second_pass_on(c, algo)) {
             ScopedTime tm(c, kKindSecondPass, fs);
+            unsigned long long *ctr = next_sp_slot(c, &tm.sp_slot);
+            tm.vertices = c->part_vb[j + 1] - c->part_vb[i0];
             CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
-                                  edges, c->part_vb[i0], c->part_vb[j + 1], c->d_extra, c->d_err, fs));
+                                  edges, c->part_vb[i0], c->part_vb[j + 1], e0, c->part_eb[j + 1],
+                                  sp_scratch(c), ctr, c->d_err, fs));
+            count_second_launch(c);
             c->stats.second_pass_vertices += c->part_vb[j + 1] - c->part_vb[i0];
         }
+        CK(cudaEventRecord(c->ev_free[slot], fs));
         f_bytes += edges * ebytes;
         ++n_tasks;
     }
@@ -1069,10 +1268,10 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             RelaxTask g{};
             g.route = kRouteC; g.mode = kModeHost; g.dst = c->m_dst; g.w = c->m_w; g.shift = 0;
             g.k_begin = cb; g.k_end = ce; g.first_entry = 0; g.device_sized = false;
-            g.src_len = c->E;
+            g.src_len = c->E; g.link_ctr = c->d_link_ctr + 2 * kRouteC;
             {
                 ScopedTime tm(c, HYTG_K_GATHER_C, c->s_c);
-                CK(launch_gather(la, dsum, g, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, 152 * 8, c->s_c));
+                CK(launch_gather(la, dsum, g, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, 8 * (int)device_sms(), c->s_c));
             }
             RelaxTask r{};
             r.route = kRouteC; r.mode = kModeCompact; r.dst = cv.cmp_dst; r.w = cv.cmp_w;
@@ -1081,7 +1280,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             r.src_len = ce - cb;
             {
                 ScopedTime tm(c, HYTG_K_RELAX_C, c->s_c);
-                CK(relax_any(c, st, la, dsum, r, 152 * 8, c->s_c));
+                CK(relax_any(c, st, la, dsum, r, 8 * (int)device_sms(), c->s_c));
             }
         }
         CK(cudaEventRecord(c->ev_c, c->s_c));
@@ -1192,6 +1391,11 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
         ck(cudaStreamCreateWithFlags(&c->s_f[i], cudaStreamNonBlocking));
         ck(cudaEventCreateWithFlags(&c->ev_f[i], cudaEventDisableTiming));
     }
+    for (int i = 0; i < kMaxSlots; ++i) {
+        ck(cudaStreamCreateWithFlags(&c->s_cp[i], cudaStreamNonBlocking));
+        ck(cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
+    }
     for (int i = 0; i < 2; ++i) ck(cudaEventCreateWithFlags(&c->ev_sum[i], cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming));
     ck(cudaEventCreateWithFlags(&c->ev_c, cudaEventDisableTiming));
@@ -1206,7 +1410,8 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_src_work, sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_bsums, 64 * sizeof(double)));
     ck(cudaMalloc(&c->d_alive, sizeof(unsigned long long)));
-    ck(cudaMalloc(&c->d_extra, sizeof(unsigned long long)));
+    ck(cudaMalloc(&c->d_sp, kSpSlots * sizeof(unsigned long long)));
+    ck(cudaMalloc(&c->d_link_ctr, 2 * kRoutes * sizeof(unsigned long long)));
     ck(cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
     ck(cudaMalloc(&c->d_loop, sizeof(LoopCtl)));
     ck(cudaMalloc(&c->d_loop_rec, (size_t)c->loop_rec_cap * sizeof(hytg_iter_record)));
@@ -1229,11 +1434,17 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_src_work);
     dfree(c->d_bsums);
     dfree(c->d_alive);
-    dfree(c->d_extra);
+    dfree(c->d_sp);
+    dfree(c->d_link_ctr);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < kMaxStreams; ++i) {
         if (c->s_f[i]) cudaStreamDestroy(c->s_f[i]);
         if (c->ev_f[i]) cudaEventDestroy(c->ev_f[i]);
+    }
+    for (int i = 0; i < kMaxSlots; ++i) {
+        if (c->s_cp[i]) cudaStreamDestroy(c->s_cp[i]);
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+        if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
     }
     for (int i = 0; i < 2; ++i) if (c->ev_sum[i]) cudaEventDestroy(c->ev_sum[i]);
     if (c->ev_bin) cudaEventDestroy(c->ev_bin);
@@ -1353,6 +1564,8 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         CK(cudaMalloc(&c->d_val, V * 4));
         CK(cudaMalloc(&c->d_delta, V * 4));
         CK(cudaMalloc(&c->d_out, V * 4));
+        CK(cudaMalloc(&c->d_sp_owner, (E / kSpChunk + 2) * 4));
+        CK(cudaMalloc(&c->d_sp_mask, c->n_words_alloc * 4));
         CK(cudaMalloc(&c->d_bm[0], c->n_words_alloc * 4));
         CK(cudaMemset(c->d_bm[0], 0, c->n_words_alloc * 4));
         CK(cudaMalloc(&c->d_ebase, V * 8));
@@ -1364,7 +1577,7 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         hytg_status s = upload_partitions(c);
         if (s != HYTG_OK) return s;
         c->vertex_bytes = (V + 1) * 8 + 3 * V * 4 + c->n_words_alloc * 4 + V * 20 + n_tiles * 4 +
-                          c->sum_dev_bytes;
+                          c->sum_dev_bytes + (E / kSpChunk + 2) * 4 + c->n_words_alloc * 4;
         if (c->weighted) {
             // automatic SSSP bucket width: 8 x the mean edge weight (delta-stepping)
             long double sw = 0;
@@ -1388,7 +1601,7 @@ hytg_status hytg_set_device_budget(hytg_ctx *c, uint64_t bytes) {
     c->carve = Carve();
     c->cache_filled_arrays = 0;
     if (bytes == 0) return fail(c, HYTG_ERR_BUDGET, "zero budget");
-    CK(cudaMalloc(&c->d_pool, bytes + 8192));
+    CK(cudaMalloc(&c->d_pool, bytes + kPoolSlack));
     c->budget = bytes;
     if (c->loaded) {
         hytg_status s = plan_carve(c, 1);
@@ -1415,6 +1628,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
         if (v < 4 || v >= 64.0 * 1024 * 1024) return bad();   // < 2^24 edges per partition
         c->part_bytes = v;
         if (c->loaded) {
+            CK(cudaSetDevice(c->device));
             c->part_edges = std::max<uint64_t>(1, (uint64_t)(v / 4));
             make_partitions(c);
             hytg_status s = upload_partitions(c);
@@ -1422,6 +1636,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
         }
     }
     else if (k == "streams") { if (v < 1 || v > kMaxStreams || v != std::floor(v)) return bad(); c->streams = v; c->carve = Carve(); }
+    else if (k == "prefetch_slots") { if (v < 0 || v > 8 || v != std::floor(v)) return bad(); c->prefetch_slots = v; c->carve = Carve(); }
     else if (k == "staging_frac") { if (v <= 0 || v >= 1) return bad(); c->staging_frac = v; c->carve = Carve(); }
     else if (k == "compact_frac") { if (v <= 0 || v >= 1) return bad(); c->compact_frac = v; c->carve = Carve(); }
     else if (k == "force_route") { if (!(v == -1 || (v >= 1 && v <= 5)) || v != std::floor(v)) return bad(); c->force_route = v; }
@@ -1437,6 +1652,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
     else if (k == "device_loop") { if (v != 0 && v != 1) return bad(); c->device_loop = v; }
+    else if (k == "serve_frames") { if (v < 0 || v > kMaxFrames || v != std::floor(v)) return bad(); c->serve_frames_param = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1452,6 +1668,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "k") *v = c->k;
     else if (k == "part_bytes") *v = c->part_bytes;
     else if (k == "streams") *v = c->streams;
+    else if (k == "prefetch_slots") *v = c->prefetch_slots;
     else if (k == "staging_frac") *v = c->staging_frac;
     else if (k == "compact_frac") *v = c->compact_frac;
     else if (k == "force_route") *v = c->force_route;
@@ -1467,6 +1684,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "compact_host") *v = c->compact_host;
     else if (k == "priority") *v = c->priority;
     else if (k == "device_loop") *v = c->device_loop;
+    else if (k == "serve_frames") *v = c->serve_frames_param;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1497,6 +1715,15 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
     }
     if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
     try {
+        if (algo == kCC) {
+            // checked once per loaded graph, on the internal arrays (hub
+            // sorting relabels vertices, which keeps symmetry)
+            if (c->symmetric < 0) c->symmetric = csr_symmetric(c->h_off, c->h_dst, c->V) ? 1 : 0;
+            if (!c->symmetric)
+                return fail(c, HYTG_ERR_ARG,
+                            "CC needs a symmetric CSR (every edge u->v with a reverse v->u of the same "
+                            "multiplicity); symmetrise the graph first");
+        }
         CK(cudaSetDevice(c->device));
         const auto t_start = std::chrono::steady_clock::now();
         c->have_result = false;
@@ -1508,7 +1735,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->batch_mode = kBatchNone;
         c->batch_K = 1;
         if (bmode != kBatchNone) {
-            hytg_status bsx = ensure_batch(c, bmode);
+            hytg_status bsx = ensure_batch(c, bmode, n_sources);
+            if (bsx == HYTG_OK) bsx = attach_own_frames(c, bmode, n_sources);
             if (bsx != HYTG_OK) return bsx;
             c->batch_mode = bmode;
             c->batch_K = n_sources;
@@ -1525,7 +1753,10 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             delta = c->sssp_delta < 0 ? c->auto_delta : (uint64_t)c->sssp_delta;
         unsigned int bucket = delta ? (unsigned int)std::min<uint64_t>(delta, 0xFFFFFFFEull) : 0xFFFFFFFFu;
         CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
-        CK(cudaMemsetAsync(c->d_extra, 0, 8, c->s_main));
+        CK(cudaMemsetAsync(c->d_sp, 0, kSpSlots * 8, c->s_main));
+        CK(cudaMemsetAsync(c->d_link_ctr, 0, 2 * kRoutes * 8, c->s_main));
+        c->sp_launches = 0;
+        c->timeline.clear();
         if ((algo == kPR || algo == kPPR) && c->d_hub_rep && c->batch_mode == kBatchNone)
             CK(cudaMemsetAsync(c->d_hub_rep, 0, (size_t)kHubReplicas * c->n_hub_rep * 4, c->s_main));
         {
@@ -1535,6 +1766,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 CK(cudaMemcpyAsync(c->d_src, src_int, sizeof(src_int), cudaMemcpyHostToDevice, c->s_main));
                 CK(cudaMemsetAsync(c->d_src_work, 0, 8, c->s_main));
                 CK(cudaMemsetAsync(c->d_overflow, 0, 4, c->s_main));
+                for (uint32_t g = 0; g * kFrameSources < c->batch_K; ++g)
+                    CK(launch_frame_init(c->bs, c->V, g, c->s_main));
                 CK(launch_b_init(c->bs, c->V, c->n_words_alloc, c->d_src, c->batch_K,
                                  (float)(1.0 - c->pr_damping), st.bm_cur, c->s_main));
             } else {
@@ -1617,7 +1850,11 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         if ((algo == kPR || algo == kPPR) && c->batch_mode == kBatchNone)
             CK(cudaMemcpyAsync(prs, c->d_prsums, 16, cudaMemcpyDeviceToHost, c->s_main));
         unsigned long long swork = 0, extra = 0;
-        CK(cudaMemcpyAsync(&extra, c->d_extra, 8, cudaMemcpyDeviceToHost, c->s_main));
+        const uint32_t n_sp = std::min<uint32_t>(c->sp_launches + 1, kSpSlots);
+        std::vector<unsigned long long> sp(n_sp, 0);
+        unsigned long long lctr[2 * kRoutes] = {};
+        CK(cudaMemcpyAsync(sp.data(), c->d_sp, n_sp * 8, cudaMemcpyDeviceToHost, c->s_main));
+        CK(cudaMemcpyAsync(lctr, c->d_link_ctr, sizeof lctr, cudaMemcpyDeviceToHost, c->s_main));
         if (c->batch_mode != kBatchNone)
             CK(cudaMemcpyAsync(&swork, c->d_src_work, 8, cudaMemcpyDeviceToHost, c->s_main));
         CK(cudaEventRecord(c->ev_run[1], c->s_main));
@@ -1633,7 +1870,16 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         c->stats.pr_rank_sum = prs[0];
         c->stats.pr_residual_sum = prs[1];
         c->stats.n_sources = c->batch_K;
+        for (unsigned long long x : sp) extra += x;
         c->stats.extra_edges = extra;
+        for (int r = 0; r < kRoutes; ++r) {
+            c->stats.link_sector_bytes[r] = lctr[2 * r] * 32ull;
+            c->stats.link_line_bytes[r] = lctr[2 * r + 1] * 128ull;
+        }
+        // explicit copies move exactly their bytes (F; C compacted on the host)
+        c->stats.link_sector_bytes[kRouteF] = c->stats.link_line_bytes[kRouteF] = c->stats.link_bytes[kRouteF];
+        if (c->compact_host > 0)
+            c->stats.link_sector_bytes[kRouteC] = c->stats.link_line_bytes[kRouteC] = c->stats.link_bytes[kRouteC];
         c->stats.source_edges = c->batch_mode != kBatchNone ? swork : c->stats.edges_relaxed;
         for (size_t i = 0; i + 1 < c->iter_ev.size(); ++i) {
             // host-issued iterations only: a mark and the next iteration's mark
@@ -1678,6 +1924,25 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             c->stats.route_busy_ms[kRouteC] = busy_of[HYTG_K_GATHER_C];
             c->stats.route_busy_ms[kRouteZ] = busy_of[HYTG_K_RELAX_Z];
         }
+        c->timeline.reserve(c->timed.size());
+        for (auto &tl : c->timed) {
+            float t0 = 0, t1 = 0;
+            if (cudaEventElapsedTime(&t0, c->ev_run[0], tl.a) != cudaSuccess ||
+                cudaEventElapsedTime(&t1, c->ev_run[0], tl.b) != cudaSuccess)
+                continue;
+            hytg_timed_launch r{};
+            r.kind = (uint32_t)tl.kind;
+            r.stream = (uint32_t)tl.stream;
+            r.start_ms = t0;
+            r.end_ms = t1;
+            r.bytes = tl.bytes;
+            r.edges = tl.edges;
+            r.vertices = tl.vertices;
+            if (tl.sp_slot >= 0)
+                r.edges = (uint32_t)tl.sp_slot < kSpSlots - 1 && (size_t)tl.sp_slot < sp.size() ? sp[tl.sp_slot]
+                                                                                            : UINT64_MAX;
+            c->timeline.push_back(r);
+        }
         for (auto &tl : c->timed) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, tl.a, tl.b) == cudaSuccess) {
@@ -1720,7 +1985,7 @@ hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
     if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
     CK(cudaSetDevice(c->device));
     const int mode = algo == kBFS ? kBatchBFS : algo == kSSSP ? kBatchSSSP : kBatchPPR;
-    hytg_status s = ensure_batch(c, mode);
+    hytg_status s = ensure_batch(c, mode, 1);
     if (s != HYTG_OK) return s;
     c->batch_mode = mode;
     c->batch_K = n_slots;
@@ -1731,8 +1996,33 @@ hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
     c->iter_ev.clear();
     c->ev_used = 0;
     const int n_arrays = algo == kSSSP ? 2 : 1;
-    s = plan_carve(c, n_arrays);
-    if (s != HYTG_OK) return s;
+    // The budget holds the edge-side carve and the queries' frames (8 queries
+    // each): as many frames as the slots can use (at most "serve_frames"),
+    // fewer if the budget cannot hold them beside the smallest edge carve.
+    const uint64_t fb = frame_bytes(c, mode);
+    const uint64_t pool_bytes = c->budget + kPoolSlack;
+    uint32_t nf = (n_slots + kFrameSources - 1) / kFrameSources;
+    if (c->serve_frames_param > 0) nf = std::min<uint32_t>(nf, (uint32_t)c->serve_frames_param);
+    for (; nf >= 1; --nf) {
+        if ((uint64_t)nf * fb + kPoolSlack >= c->budget) continue;
+        const uint64_t eb = c->budget - (uint64_t)nf * fb - kPoolSlack;
+        if (plan_carve(c, n_arrays, eb) != HYTG_OK) continue;
+        const uint64_t base = (c->carve.end + 255) & ~uint64_t(255);
+        if (base + (uint64_t)nf * fb > pool_bytes) continue;
+        c->serve_frame_base = (char *)c->d_pool + base;
+        c->serve_edge_budget = eb;
+        break;
+    }
+    if (nf == 0) {
+        c->batch_mode = kBatchNone;
+        c->carve = Carve();
+        return fail(c, HYTG_ERR_BUDGET, "the device budget holds no query frame (" + std::to_string(fb) +
+                                            " B for 8 queries) beside the smallest edge-side carve");
+    }
+    c->serve_frames = nf;
+    c->serve_frame_bytes = fb;
+    c->serve_frames_used = 0;
+    for (auto &f : c->serve_group_frame) f = -1;
     s = ensure_cache(c, n_arrays);
     if (s != HYTG_OK) return s;
     CK(cudaMemsetAsync(c->d_err, 0, 4, c->s_main));
@@ -1753,6 +2043,21 @@ hytg_status hytg_serve_admit(hytg_ctx *c, uint32_t slot, uint32_t source) {
     if (slot >= c->batch_K) return fail(c, HYTG_ERR_ARG, "slot out of range");
     if (c->serve_busy & (1ull << slot)) return fail(c, HYTG_ERR_STATE, "slot is busy");
     if (source >= c->V) return fail(c, HYTG_ERR_ARG, "source out of range");
+    CK(cudaSetDevice(c->device));
+    const uint32_t g = slot / kFrameSources;
+    if (c->serve_group_frame[g] < 0) {
+        // the slot's group of 8 needs a frame of device memory for its state
+        int f = -1;
+        for (uint32_t i = 0; i < c->serve_frames && f < 0; ++i)
+            if (!((c->serve_frames_used >> i) & 1u)) f = (int)i;
+        if (f < 0)
+            return fail(c, HYTG_ERR_BUDGET, "no device memory free for the query's state: every frame of "
+                                            "the budget is in use (admit it when a query finishes)");
+        c->serve_frames_used |= 1u << f;
+        c->serve_group_frame[g] = f;
+        set_group_frame(c, g, c->serve_frame_base + (uint64_t)f * c->serve_frame_bytes);
+        CK(launch_frame_init(c->bs, c->V, g, c->s_main));
+    }
     const uint32_t src = c->permuted ? c->h_inv[source] : source;
     CK(launch_serve_admit(c->bs, c->V, slot, src, (float)(1.0 - c->pr_damping), c->d_bm[0], c->s_main));
     c->serve_busy |= 1ull << slot;
@@ -1763,6 +2068,7 @@ hytg_status hytg_serve_admit(hytg_ctx *c, uint32_t slot, uint32_t source) {
 hytg_status hytg_serve_step(hytg_ctx *c, uint64_t *finished, uint64_t *busy) {
     if (!c) return HYTG_ERR_ARG;
     if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    CK(cudaSetDevice(c->device));
     try {
         const int algo = c->serve_algo;
         const int n_arrays = algo == kSSSP ? 2 : 1;
@@ -1795,6 +2101,7 @@ hytg_status hytg_serve_fetch(hytg_ctx *c, uint32_t slot, void *out, uint64_t out
     if (!(c->serve_busy & bit) || (c->serve_alive & bit))
         return fail(c, HYTG_ERR_STATE, "slot has no finished query");
     if (out_bytes < c->V * 4) return fail(c, HYTG_ERR_ARG, "output buffer too small");
+    CK(cudaSetDevice(c->device));
     CK(launch_serve_extract(c->bs, c->V, slot, c->d_perm, c->serve_admit_it[slot], c->d_bout,
                             c->d_bsums, c->s_main));
     CK(cudaMemcpyAsync(out, c->d_bout, c->V * 4, cudaMemcpyDeviceToHost, c->s_main));
@@ -1803,6 +2110,7 @@ hytg_status hytg_serve_fetch(hytg_ctx *c, uint32_t slot, void *out, uint64_t out
     CK(cudaMemcpyAsync(&ierr, c->d_err, 4, cudaMemcpyDeviceToHost, c->s_main));
     CK(cudaStreamSynchronize(c->s_main));
     c->serve_busy &= ~bit;
+    release_idle_frame(c, slot / kFrameSources);
     if (ierr) return fail(c, HYTG_ERR_CUDA, "internal index check failed");
     if (ovf) return fail(c, HYTG_ERR_OVERFLOW, "an SSSP distance does not fit in 32 bits");
     return HYTG_OK;
@@ -1811,10 +2119,26 @@ hytg_status hytg_serve_fetch(hytg_ctx *c, uint32_t slot, void *out, uint64_t out
 hytg_status hytg_serve_end(hytg_ctx *c) {
     if (!c) return HYTG_ERR_ARG;
     if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->s_main));
     c->serving = false;
-    c->batch_mode = kBatchNone;
     c->serve_busy = 0;
+    for (uint32_t g = 0; g < kMaxFrames; ++g) release_idle_frame(c, g);
+    c->batch_mode = kBatchNone;
+    return HYTG_OK;
+}
+
+hytg_status hytg_serve_get_info(hytg_ctx *c, hytg_serve_info *out) {
+    if (!c || !out) return HYTG_ERR_ARG;
+    if (!c->serving) return fail(c, HYTG_ERR_STATE, "not serving");
+    hytg_serve_info i{};
+    i.frames = c->serve_frames;
+    i.frames_free = c->serve_frames - (uint32_t)__builtin_popcount(c->serve_frames_used);
+    i.slots_per_frame = kFrameSources;
+    i.frame_bytes = c->serve_frame_bytes;
+    i.edge_budget_bytes = c->serve_edge_budget;
+    i.busy_slots = c->serve_busy;
+    *out = i;
     return HYTG_OK;
 }
 
@@ -1972,7 +2296,7 @@ hytg_status hytg_probe_link(hytg_ctx *c, uint64_t bytes, uint32_t reps, double *
         best = 1e30f;
         for (uint32_t r = 0; r < reps + 1; ++r) {
             CK(cudaEventRecord(a, c->s_main));
-            CK(launch_zc_probe((const uint4 *)mp, bytes / 16, sink, 152 * 8, c->s_main));
+            CK(launch_zc_probe((const uint4 *)mp, bytes / 16, sink, 8 * (int)device_sms(), c->s_main));
             CK(cudaEventRecord(b, c->s_main));
             CK(cudaEventSynchronize(b));
             float ms;
@@ -2029,11 +2353,65 @@ hytg_status hytg_probe_atomics(hytg_ctx *c, uint64_t n, uint32_t reps, double *u
     return st;
 }
 
+hytg_status hytg_probe_atomics_hub(hytg_ctx *c, uint64_t n, uint32_t reps, uint32_t n_rep,
+                                   double *plain_gops, double *replica_gops) {
+    if (!c || n < 1024 || n > (1ull << 30) || reps == 0 || n_rep > (1u << 20)) return HYTG_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    unsigned int *idx = nullptr;
+    float *d = nullptr, *rp = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto run = [&]() -> hytg_status {
+        CK(cudaMalloc(&idx, n * 4));
+        CK(cudaMalloc(&d, (1ull << 24) * 4));
+        CK(cudaMemset(d, 0, (1ull << 24) * 4));
+        if (n_rep) {
+            CK(cudaMalloc(&rp, (size_t)kHubReplicas * n_rep * 4));
+            CK(cudaMemset(rp, 0, (size_t)kHubReplicas * n_rep * 4));
+        }
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(launch_red_probe(idx, d, n, 2, true, c->s_main));
+        for (int with_rep = 0; with_rep < 2; ++with_rep) {
+            float best = 1e30f;
+            for (uint32_t r = 0; r < reps + 1; ++r) {
+                CK(cudaEventRecord(a, c->s_main));
+                CK(launch_red_probe(idx, d, n, 2, false, c->s_main, with_rep ? rp : nullptr,
+                                    with_rep ? n_rep : 0));
+                CK(cudaEventRecord(b, c->s_main));
+                CK(cudaEventSynchronize(b));
+                float ms;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (r > 0) best = std::min(best, ms);
+            }
+            double *out = with_rep ? replica_gops : plain_gops;
+            if (out) *out = n / (best * 1e-3) / 1e9;
+        }
+        return HYTG_OK;
+    };
+    hytg_status st = run();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (idx) cudaFree(idx);
+    if (d) cudaFree(d);
+    if (rp) cudaFree(rp);
+    return st;
+}
+
 hytg_status hytg_get_permutation(hytg_ctx *c, uint32_t *perm, uint64_t V) {
     if (!c || !perm) return HYTG_ERR_ARG;
     if (!c->loaded) return fail(c, HYTG_ERR_STATE, "no graph loaded");
     if (V < c->V) return fail(c, HYTG_ERR_ARG, "buffer too small");
     for (uint64_t n = 0; n < c->V; ++n) perm[n] = c->permuted ? c->h_perm[n] : (uint32_t)n;
+    return HYTG_OK;
+}
+
+hytg_status hytg_get_timeline(hytg_ctx *c, hytg_timed_launch *out, uint32_t cap, uint32_t *n) {
+    if (!c || !n) return HYTG_ERR_ARG;
+    *n = (uint32_t)c->timeline.size();
+    if (out) {
+        const uint32_t k = std::min<uint32_t>(cap, *n);
+        std::copy(c->timeline.begin(), c->timeline.begin() + k, out);
+    }
     return HYTG_OK;
 }
 

@@ -79,7 +79,7 @@ __global__ void k_loop_decide(const Summary *sum, LoopCtl *ctl, cudaGraphConditi
 cudaError_t launch_zero_u64(unsigned long long *p, unsigned long long n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     unsigned long long blocks = (n + 255) / 256;
-    if (blocks > 152ull * 4) blocks = 152ull * 4;
+    if (blocks > 4ull * device_sms()) blocks = 4ull * device_sms();
     k_zero_u64<<<(unsigned int)blocks, 256, 0, s>>>(p, n);
     return cudaGetLastError();
 }

@@ -1,5 +1,7 @@
 // Initialisation, PageRank finalisation, frontier upload and the host-link
 // probe kernel.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace hytg {
@@ -37,9 +39,11 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
     if (t0 == 0) *st.overflow = 0u;
 }
 
-// Delta-PageRank frontier: v is active iff delta[v] > eps (Sec. VI-A, with
-// the threshold reading of the design notes).  Inactive vertices always hold
-// delta <= eps, so this equals "delta crossed eps during the iteration".
+// Delta-PageRank frontier: v is active iff delta[v] > eps (Sec. VI-A names
+// delta-based PageRank without a threshold; eps is an FP32 residual on the
+// unnormalised scale, where every vertex starts with delta = 1 - d).
+// Inactive vertices always hold delta <= eps, so this equals "delta crossed
+// eps during the iteration".
 __global__ void k_pr_frontier(AlgoState st, unsigned long long V, unsigned long long n_words_alloc) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -81,11 +85,27 @@ __global__ void k_cc_jump(AlgoState st, unsigned long long n_words_alloc) {
 
 // CC labels (smallest internal id of each component) to the smallest
 // original id of the component, in original vertex order.
+// tmp[label] = smallest original id with that label.  Most vertices share
+// the giant component's label, so a warp whose 32 vertices all carry one
+// label reduces their ids first and issues one atomic instead of 32 to the
+// same address.
 __global__ void k_cc_min_orig(AlgoState st, unsigned long long V, unsigned int *tmp) {
+    const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
-         v += stride)
-        atomicMin(&tmp[st.val[v]], st.perm ? st.perm[v] : (unsigned int)v);
+    for (unsigned long long base = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull;
+         base < V; base += stride) {
+        const unsigned long long v = base + lane;
+        const bool in = v < V;
+        const unsigned int lab = in ? st.val[v] : 0xFFFFFFFFu;
+        const unsigned int orig = in ? (st.perm ? st.perm[v] : (unsigned int)v) : 0xFFFFFFFFu;
+        const unsigned int lab0 = __shfl_sync(0xffffffffu, lab, 0);      // lane 0 is in range
+        if (__all_sync(0xffffffffu, !in || lab == lab0)) {
+            const unsigned int m = __reduce_min_sync(0xffffffffu, orig);
+            if (lane == 0) atomicMin(&tmp[lab0], m);
+        } else if (in) {
+            atomicMin(&tmp[lab], orig);
+        }
+    }
 }
 __global__ void k_cc_write(AlgoState st, unsigned long long V, const unsigned int *tmp,
                            unsigned int *out) {
@@ -191,6 +211,27 @@ __device__ __forceinline__ unsigned long long probe_mix(unsigned long long x) {
     x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
     return x;
 }
+__device__ __forceinline__ unsigned int binom24(unsigned int n, unsigned int r) {
+    if (r > n) return 0u;
+    unsigned long long x = 1;
+    for (unsigned int i = 1; i <= r; ++i) x = x * (n - r + i) / i;
+    return (unsigned int)x;
+}
+// The same skew after hub sorting: ids ordered by their probability, i.e.
+// by popcount (fewer set bits first), and within one popcount by the
+// combinatorial rank of the bit pattern.  Bijective on [0, 2^24).
+__device__ __forceinline__ unsigned int hub_rank24(unsigned int v) {
+    const unsigned int k = __popc(v);
+    unsigned int off = 0;
+    for (unsigned int i = 0; i < k; ++i) off += binom24(24, i);
+    unsigned int rank = 0, seen = 0;
+    for (unsigned int b = 0; b < 24; ++b)
+        if ((v >> b) & 1u) rank += binom24(b, ++seen);
+    return off + rank;
+}
+
+// skew 0: uniform over 2^24 floats; 1: R-MAT in-degree skew (each of 24
+// index bits set with probability 0.24); 2: that skew with hub-sorted ids.
 __global__ void k_probe_idx(unsigned int *idx, unsigned long long n, int skew) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -200,6 +241,7 @@ __global__ void k_probe_idx(unsigned int *idx, unsigned long long n, int skew) {
         } else {
             for (int j = 0; j < 24; ++j)
                 if ((probe_mix(i * 64 + j + 12345) & 0xFFFFFFFFull) < 1030792151ull) v |= 1u << j;
+            if (skew == 2) v = hub_rank24(v);
         }
         idx[i] = v;
     }
@@ -209,14 +251,45 @@ __global__ void k_probe_red(const unsigned int *__restrict__ idx, unsigned long 
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride)
         atomicAdd(&d[__ldg(idx + i)], 1.0f);
 }
+// The relax kernels' scheme: additions to ids below n_rep go to this SM's
+// row of per-SM replicas (not folded here).
+__global__ void k_probe_red_rep(const unsigned int *__restrict__ idx, unsigned long long n, float *d,
+                                float *rep, unsigned int n_rep) {
+    unsigned int smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    float *row = rep + (size_t)(smid % kHubReplicas) * n_rep;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned int v = __ldg(idx + i);
+        if (v < n_rep) atomicAdd(&row[v], 1.0f);
+        else atomicAdd(&d[v], 1.0f);
+    }
+}
 
 inline unsigned int grid_for(unsigned long long n, unsigned int block) {
     unsigned long long g = (n + block - 1) / block;
-    if (g > 152ull * 32) g = 152ull * 32;
+    const unsigned long long cap = 32ull * device_sms();
+    if (g > cap) g = cap;
     return g == 0 ? 1u : (unsigned int)g;
 }
 
+constexpr int kMaxDevices = 64;
+std::atomic<unsigned int> g_sms[kMaxDevices];
+
 }  // namespace
+
+unsigned int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    unsigned int n = g_sms[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+        n = (unsigned int)v;
+        g_sms[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
 
 cudaError_t launch_init(const AlgoState &st, unsigned long long V, unsigned long long n_words_alloc,
                         unsigned int source, cudaStream_t s) {
@@ -258,7 +331,7 @@ cudaError_t launch_pr_frontier(const AlgoState &st, unsigned long long V,
                                unsigned long long n_words_alloc, cudaStream_t s) {
     const unsigned long long n = n_words_alloc * 32;
     unsigned long long g = (n + 255) / 256;
-    if (g > 152ull * 16) g = 152ull * 16;
+    if (g > 16ull * device_sms()) g = 16ull * device_sms();
     k_pr_frontier<<<(unsigned int)g, 256, 0, s>>>(st, V, n_words_alloc);
     return cudaGetLastError();
 }
@@ -277,9 +350,10 @@ cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *
 }
 
 cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, int skew, bool gen,
-                             cudaStream_t s) {
-    if (gen) k_probe_idx<<<152 * 16, 256, 0, s>>>(idx, n, skew);
-    else k_probe_red<<<152 * 32, 256, 0, s>>>(idx, n, d);
+                             cudaStream_t s, float *rep, unsigned int n_rep) {
+    if (gen) k_probe_idx<<<16 * device_sms(), 256, 0, s>>>(idx, n, skew);
+    else if (rep && n_rep) k_probe_red_rep<<<32 * device_sms(), 256, 0, s>>>(idx, n, d, rep, n_rep);
+    else k_probe_red<<<32 * device_sms(), 256, 0, s>>>(idx, n, d);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ __global__ void k_na_select(const NoAllocScratch *sc, unsigned int n_parts,
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mutex;
 void *g_na_addr[kNaMaxDevices] = {};
+unsigned int g_na_sms[kNaMaxDevices] = {};
 
 }  // namespace
 }  // namespace hytg
@@ -121,18 +122,28 @@ extern "C" hytg_status hytg_plan_noalloc(hytg_algo algo, const uint32_t *frontie
         return HYTG_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return HYTG_ERR_CUDA;
+    // an error left pending by earlier, unrelated work is not this call's to
+    // report or to clear: queue nothing and leave it for its owner
+    if (cudaPeekAtLastError() != cudaSuccess) return HYTG_ERR_CUDA;
     void *scratch = nullptr;
+    unsigned int sms = 0;
     {
+        // once per device, with that device current: the device address of
+        // the static scratch array and the SM count that sizes the grid
         std::lock_guard<std::mutex> lock(g_na_mutex);
         if (!g_na_addr[dev]) {
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            int n = 0;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+                cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
                 cudaGetLastError();
                 return HYTG_ERR_CUDA;
             }
+            g_na_sms[dev] = (unsigned int)n;
             g_na_addr[dev] = p;
         }
         scratch = g_na_addr[dev];
+        sms = g_na_sms[dev];
     }
     CostParams cp;
     auto q = [](double x) { return (unsigned long long)((x * (double)kParamDen) + 0.5); };
@@ -155,7 +166,7 @@ extern "C" hytg_status hytg_plan_noalloc(hytg_algo algo, const uint32_t *frontie
                                    (unsigned long long *)counts);
     const unsigned long long n_groups = ((V + 31) / 32 + 31) / 32;
     unsigned long long blocks = (n_groups + 7) / 8;
-    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    if (blocks > 16ull * sms) blocks = 16ull * sms;
     if (blocks == 0) blocks = 1;
     k_na_count<<<(unsigned int)blocks, 256, 0, s>>>(frontier, V, (const unsigned long long *)offsets, sc,
                                                     n_parts, a == kSSSP ? 2u : 1u, prm.m,

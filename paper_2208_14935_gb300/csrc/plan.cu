@@ -420,7 +420,7 @@ unsigned long long resident_blocks(K kernel) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
         sms <= 0 || per_sm <= 0)
-        return 152ull * 2;
+        return 2ull * device_sms();
     return (unsigned long long)sms * (unsigned long long)per_sm;
 }
 

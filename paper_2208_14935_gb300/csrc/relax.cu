@@ -68,6 +68,7 @@ __device__ __forceinline__ void relax_tile(const AlgoState &st, const ListArrays
     const bool weighted = (ALGO == kSSSP);
     unsigned long long k0;
     const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
+    if (t.link_ctr) count_link_reads<false>(sm, k0, n, weighted ? 2u : 1u, t.link_ctr);
     unsigned int dv[kRelaxIPT], wv[kRelaxIPT], pv[kRelaxIPT];
 #pragma unroll
     for (int j = 0; j < kRelaxIPT; ++j) {
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Sum
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
         unsigned long long k0;
         const int n = tile_setup<false>(sm, la, sum, t, tile, kb, ke, &k0);
+        if (t.link_ctr) count_link_reads<false>(sm, k0, n, out_w ? 2u : 1u, t.link_ctr);
         unsigned int dv[kRelaxIPT], wv[kRelaxIPT];
 #pragma unroll
         for (int j = 0; j < kRelaxIPT; ++j) {
@@ -172,11 +174,15 @@ __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Sum
 // during this iteration (PageRank: delta > eps; others: frontier bit set and,
 // for bucketed SSSP, dist below the bucket) are taken and pushed along their
 // edges in `dst`/`w`, which hold CSR edges [shift, shift + src_len).
-// A warp takes 32 consecutive vertices; vertices with more than
-// kSecondPassMaxDeg edges are not taken and stay active for the next
-// iteration's load-balanced relax.
-constexpr unsigned long long kSecondPassMaxDeg = 4096;
-
+//
+// Two launches, so that the work is balanced over edges whatever the
+// degrees: k_sp_take (a warp per 32 consecutive vertices) takes the vertices,
+// records each one's push value and a taken bit, and writes for every chunk
+// of kSpChunk edges whose first edge lies in a vertex's list that vertex as
+// the chunk's owner; k_sp_push gives each warp whole chunks of the range's
+// edges [E0, E1), finds each edge's owner among a window of 32 consecutive
+// vertices (their list starts, by shuffles) and pushes the edges of taken
+// owners with coalesced loads.
 template <int ALGO>
 __device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned long long v,
                                                  unsigned long long deg, unsigned int &pay) {
@@ -200,100 +206,132 @@ __device__ __forceinline__ bool second_pass_take(const AlgoState &st, unsigned l
         const unsigned int old = atomicAnd(&st.bm_cur[v >> 5], ~mask);
         if (!(old & mask)) return false;
         pay = __ldcg(&st.val[v]);
-        return true;
+        return deg > 0;
     }
 }
 
 template <int ALGO>
-__global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigned long long *off,
-                                                     const unsigned int *dst, const unsigned int *w,
-                                                     long long shift, unsigned long long src_len,
-                                                     unsigned long long vlo, unsigned long long vhi,
-                                                     unsigned long long *edges_out, unsigned int *err) {
+__global__ void __launch_bounds__(256) k_sp_take(AlgoState st, const unsigned long long *off,
+                                                 unsigned long long vlo, unsigned long long vhi,
+                                                 SecondPassScratch sc, unsigned long long *edges_out) {
     if (st.loop) {
         if (!st.loop->work) return;
         st.bucket_limit = st.loop->bucket;
     }
-    float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
     const int lane = threadIdx.x & 31;
     unsigned long long done = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const unsigned long long first = vlo + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull);
-    for (unsigned long long base = first; base < vhi; base += stride) {
+    // vlo is a multiple of 32 (partition bounds), so each warp's 32 vertices
+    // fill one word of the taken mask
+    for (unsigned long long base = vlo + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull);
+         base < vhi; base += stride) {
         const unsigned long long v = base + lane;
-        unsigned long long e0 = ~0ull, deg = 0;       // lanes past vhi own no edge
+        unsigned long long e0 = 0, deg = 0;
         unsigned int pay = 0;
         bool mine = false;
         if (v < vhi) {
             e0 = off[v];
             deg = off[v + 1] - e0;
-            if (deg <= kSecondPassMaxDeg) mine = second_pass_take<ALGO>(st, v, deg, pay);
+            mine = second_pass_take<ALGO>(st, v, deg, pay);
+            sc.pay[v] = pay;
         }
-        const unsigned int mask = __ballot_sync(0xffffffffu, mine);
-        if (mask == 0) continue;                       // warp-uniform
-        const unsigned long long act = warp_sum_u64(mine ? deg : 0ull);
-        if (lane == 0) done += act;
-        // The 32 vertices are consecutive, so their lists form one CSR range
-        // [E0, E1).  If at least half of it belongs to taken vertices, the
-        // warp streams the range with coalesced loads and each lane finds the
-        // owner of its edge among the 32 list starts; otherwise it walks the
-        // taken vertices one at a time.
-        const int last = (int)((vhi - 1 - base) < 31 ? (vhi - 1 - base) : 31);
-        const unsigned long long E0 = __shfl_sync(0xffffffffu, e0, 0);
-        const unsigned long long E1 = __shfl_sync(0xffffffffu, e0 + deg, last);
-        if (2 * act >= E1 - E0) {
-            // kStream chunks of 32 edges per round: owners and loads of all
-            // chunks first, then the pushes, so the loads overlap
-            constexpr int kStream = 4;
-            for (unsigned long long c0 = E0; c0 < E1; c0 += 32 * kStream) {
-                unsigned int dv[kStream], wv[kStream], pv[kStream];
-                bool ok[kStream];
-#pragma unroll
-                for (int q = 0; q < kStream; ++q) {
-                    const unsigned long long k = c0 + 32 * q + lane;
-                    int own = 0;                       // largest lane whose list starts at or before k
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const unsigned long long cand = __shfl_sync(0xffffffffu, e0, own + step);
-                        if (cand <= k) own += step;
-                    }
-                    pv[q] = __shfl_sync(0xffffffffu, pay, own);
-                    ok[q] = k < E1 && ((mask >> own) & 1u);
-                    dv[q] = 0;
-                    wv[q] = 0;
-                    if (ok[q]) {
-                        const long long i = (long long)k - shift;
-                        if (i < 0 || (unsigned long long)i >= src_len) {
-                            atomicOr(err, 16u);
-                            ok[q] = false;
-                        } else {
-                            dv[q] = __ldg(dst + i);
-                            if (ALGO == kSSSP) wv[q] = __ldg(w + i);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kStream; ++q)
-                    if (ok[q]) relax_edge<ALGO>(st, dv[q], pv[q], wv[q], hub_rep);
-            }
-        } else {
-            unsigned int m = mask;
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const unsigned long long ce0 = __shfl_sync(0xffffffffu, e0, src);
-                const unsigned long long cdeg = __shfl_sync(0xffffffffu, deg, src);
-                const unsigned int cpay = __shfl_sync(0xffffffffu, pay, src);
-                for (unsigned long long k = lane; k < cdeg; k += 32) {
-                    const long long i = (long long)(ce0 + k) - shift;
-                    if (i < 0 || (unsigned long long)i >= src_len) { atomicOr(err, 16u); break; }
-                    relax_edge<ALGO>(st, __ldg(dst + i), cpay, (ALGO == kSSSP) ? __ldg(w + i) : 0u, hub_rep);
-                }
-            }
+        const unsigned int taken = __ballot_sync(0xffffffffu, mine);
+        if (lane == 0) sc.mask[base >> 5] = taken;
+        done += mine ? deg : 0ull;
+        // owners of the chunks [c_beg, c_end) whose first edge is in v's list,
+        // written by the whole warp one vertex at a time
+        const unsigned long long c_beg = deg ? (e0 + kSpChunk - 1) / kSpChunk : 0ull;
+        const unsigned long long c_end = deg ? (e0 + deg - 1) / kSpChunk + 1 : 0ull;
+        unsigned int has = __ballot_sync(0xffffffffu, c_end > c_beg);
+        while (has) {
+            const int l = __ffs(has) - 1;
+            has &= has - 1;
+            const unsigned long long cb = __shfl_sync(0xffffffffu, c_beg, l);
+            const unsigned long long ce = __shfl_sync(0xffffffffu, c_end, l);
+            for (unsigned long long c = cb + lane; c < ce; c += 32) sc.owner[c] = (unsigned int)(base + l);
         }
     }
     done = warp_sum_u64(done);
     if (lane == 0 && done) atomicAdd(edges_out, done);
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_sp_push(AlgoState st, const unsigned long long *off,
+                                                 const unsigned int *dst, const unsigned int *w,
+                                                 long long shift, unsigned long long src_len,
+                                                 unsigned long long vlo, unsigned long long vhi,
+                                                 unsigned long long E0, unsigned long long E1,
+                                                 SecondPassScratch sc, unsigned int *err) {
+    if (st.loop && !st.loop->work) return;
+    if (E1 <= E0) return;
+    float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long c_first = E0 / kSpChunk, c_last = (E1 - 1) / kSpChunk;
+    for (unsigned long long c = c_first + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5);
+         c <= c_last; c += nwarps) {
+        const unsigned long long k0 = c * kSpChunk > E0 ? c * kSpChunk : E0;
+        const unsigned long long k1 = (c + 1) * kSpChunk < E1 ? (c + 1) * kSpChunk : E1;
+        // a vertex at or before the owner of k0: the recorded owner of the
+        // chunk's first edge, or vlo for a chunk that starts before the range
+        unsigned long long u0 = c * kSpChunk >= E0 ? (unsigned long long)sc.owner[c] : vlo;
+        if (u0 < vlo || u0 >= vhi) {
+            if (lane == 0) atomicOr(err, 32u);
+            continue;
+        }
+        unsigned long long kb = k0;
+        while (kb < k1) {
+            // window of 32 candidate owners u0 .. u0 + 31 (past vhi: no edges)
+            const unsigned long long u = u0 + lane;
+            const unsigned long long su = u < vhi ? off[u] : E1;
+            const unsigned long long ue = u0 + 32 < vhi ? u0 + 32 : vhi;
+            const unsigned long long wend_all = off[ue];       // end of the window's edges
+            const bool tk = u < vhi && ((sc.mask[u >> 5] >> (u & 31)) & 1u);
+            const unsigned int pay = tk ? sc.pay[u] : 0u;
+            const unsigned int tmask = __ballot_sync(0xffffffffu, tk);
+            const unsigned long long wend = wend_all < k1 ? wend_all : k1;
+            if (tmask) {
+                constexpr int kStream = 4;
+                for (unsigned long long r0 = kb; r0 < wend; r0 += 32 * kStream) {
+                    unsigned int dv[kStream], wv[kStream], pv[kStream];
+                    bool ok[kStream];
+#pragma unroll
+                    for (int q = 0; q < kStream; ++q) {
+                        const unsigned long long k = r0 + 32 * q + lane;
+                        int own = 0;                   // largest lane whose list starts at or before k
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const unsigned long long cand = __shfl_sync(0xffffffffu, su, own + step);
+                            if (cand <= k) own += step;
+                        }
+                        pv[q] = __shfl_sync(0xffffffffu, pay, own);
+                        ok[q] = k < wend && ((tmask >> own) & 1u);
+                        dv[q] = 0;
+                        wv[q] = 0;
+                        if (ok[q]) {
+                            const long long i = (long long)k - shift;
+                            if (i < 0 || (unsigned long long)i >= src_len) {
+                                atomicOr(err, 16u);
+                                ok[q] = false;
+                            } else {
+                                dv[q] = __ldg(dst + i);
+                                if (ALGO == kSSSP) wv[q] = __ldg(w + i);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kStream; ++q)
+                        if (ok[q]) relax_edge<ALGO>(st, dv[q], pv[q], wv[q], hub_rep);
+                }
+            }
+            if (wend <= kb && ue >= vhi) {          // no vertex left to own kb: inconsistent offsets
+                if (lane == 0) atomicOr(err, 32u);
+                break;
+            }
+            if (wend > kb) kb = wend;
+            u0 += 32;
+        }
+    }
 }
 
 }  // namespace
@@ -301,16 +339,35 @@ __global__ void __launch_bounds__(256) k_second_pass(AlgoState st, const unsigne
 cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *off,
                                const unsigned int *dst, const unsigned int *w, long long shift,
                                unsigned long long src_len, unsigned long long vlo,
-                               unsigned long long vhi, unsigned long long *edges_out,
+                               unsigned long long vhi, unsigned long long E0, unsigned long long E1,
+                               const SecondPassScratch &sc, unsigned long long *edges_out,
                                unsigned int *err, cudaStream_t s) {
     if (vhi <= vlo) return cudaSuccess;
-    unsigned long long blocks = (vhi - vlo + 255) / 256;
-    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    if (vlo & 31) return cudaErrorInvalidValue;          // ranges start on a mask word
+    const unsigned long long cap = 8ull * device_sms();
+    unsigned long long tb = (vhi - vlo + 255) / 256;
+    if (tb > cap) tb = cap;
+    const unsigned long long chunks = E1 > E0 ? (E1 - 1) / kSpChunk - E0 / kSpChunk + 1 : 0ull;
+    unsigned long long pb = (chunks + 7) / 8;            // one chunk per warp per round
+    if (pb > cap) pb = cap;
+    if (pb == 0) pb = 1;
     switch (st.algo) {
-        case kBFS: k_second_pass<kBFS><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
-        case kSSSP: k_second_pass<kSSSP><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
-        case kCC: k_second_pass<kCC><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
-        default: k_second_pass<kPR><<<(unsigned int)blocks, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, edges_out, err); break;
+        case kBFS:
+            k_sp_take<kBFS><<<(unsigned int)tb, 256, 0, s>>>(st, off, vlo, vhi, sc, edges_out);
+            k_sp_push<kBFS><<<(unsigned int)pb, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, E0, E1, sc, err);
+            break;
+        case kSSSP:
+            k_sp_take<kSSSP><<<(unsigned int)tb, 256, 0, s>>>(st, off, vlo, vhi, sc, edges_out);
+            k_sp_push<kSSSP><<<(unsigned int)pb, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, E0, E1, sc, err);
+            break;
+        case kCC:
+            k_sp_take<kCC><<<(unsigned int)tb, 256, 0, s>>>(st, off, vlo, vhi, sc, edges_out);
+            k_sp_push<kCC><<<(unsigned int)pb, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, E0, E1, sc, err);
+            break;
+        default:
+            k_sp_take<kPR><<<(unsigned int)tb, 256, 0, s>>>(st, off, vlo, vhi, sc, edges_out);
+            k_sp_push<kPR><<<(unsigned int)pb, 256, 0, s>>>(st, off, dst, w, shift, src_len, vlo, vhi, E0, E1, sc, err);
+            break;
     }
     return cudaGetLastError();
 }

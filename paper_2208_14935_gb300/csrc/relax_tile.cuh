@@ -113,5 +113,42 @@ __device__ __forceinline__ int tile_setup(TileSmem<BATCH> &sm, const ListArrays 
     return n_slots;
 }
 
+// Host-link reads of one tile, for routes that read mapped host memory: the
+// distinct 32-byte sectors and 128-byte lines that the tile's edges occupy in
+// one 4-byte edge array (base 256-byte aligned, so edge e sits in sector e / 8
+// and line e / 32).  A tile's edges are at increasing addresses, so a sector
+// (line) is new where it differs from the previous slot's; the first slot of
+// a tile always counts, so a sector shared with the previous tile is counted
+// twice (at most one per 2,048 edges).  Adds n_arrays times the counts to
+// ctr[0] (sectors) and ctr[1] (lines).
+template <bool BATCH>
+__device__ __forceinline__ void count_link_reads(const TileSmem<BATCH> &sm, unsigned long long k0, int n,
+                                                 unsigned int n_arrays, unsigned long long *ctr) {
+    unsigned int sec = 0, ln = 0;
+#pragma unroll
+    for (int j = 0; j < kRelaxIPT; ++j) {
+        const int slot = threadIdx.x + j * kRelaxBlock;
+        if (slot < n) {
+            const long long e = (long long)(k0 + slot) + sm.delta[sm.sid[slot]];
+            if (slot == 0) {
+                ++sec;
+                ++ln;
+            } else {
+                const long long p = (long long)(k0 + slot - 1) + sm.delta[sm.sid[slot - 1]];
+                sec += (e >> 3) != (p >> 3);
+                ln += (e >> 5) != (p >> 5);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sec += __shfl_xor_sync(0xffffffffu, sec, o);
+        ln += __shfl_xor_sync(0xffffffffu, ln, o);
+    }
+    if ((threadIdx.x & 31) == 0 && sec) {
+        atomicAdd(&ctr[0], (unsigned long long)sec * n_arrays);
+        atomicAdd(&ctr[1], (unsigned long long)ln * n_arrays);
+    }
+}
 
 }  // namespace hytg

@@ -25,6 +25,7 @@ ROUTE_NAMES = ["none", "cache", "F", "C", "Z"]
 UNREACHED = 0xFFFFFFFF
 KERNEL_KINDS = ["init", "plan", "bin", "relax_cache", "relax_F", "gather_C", "relax_C", "relax_Z",
                 "copy_F", "final", "cache_fill", "other"]
+K_SECOND_PASS = 12                      # timeline kind of a second pass
 ALGOS = {"bfs": HYTG_BFS, "sssp": HYTG_SSSP, "cc": HYTG_CC, "pagerank": HYTG_PAGERANK,
          "ppr": HYTG_PPR}
 
@@ -41,7 +42,8 @@ class hytg_stats(ctypes.Structure):
                 ("source_edges", u64), ("n_sources", u32), ("pad_", u32), ("extra_edges", u64),
                 ("host_compact_ms", dbl), ("graph_launches", u64), ("graph_iterations", u64),
                 ("second_pass_ms", dbl), ("second_pass_count", u64), ("second_pass_vertices", u64),
-                ("route_busy_ms", dbl * 5), ("kernel_busy_ms", dbl * 13)]
+                ("route_busy_ms", dbl * 5), ("kernel_busy_ms", dbl * 13),
+                ("link_sector_bytes", u64 * 5), ("link_line_bytes", u64 * 5)]
 
 
 class hytg_info(ctypes.Structure):
@@ -55,6 +57,16 @@ class hytg_iter_record(ctypes.Structure):
     _fields_ = [("active_vertices", u64), ("active_edges", u64), ("route_partitions", u32 * 5),
                 ("f_tasks", u32), ("route_edges", u64 * 5), ("link_bytes", u64),
                 ("device_ms", dbl)]
+
+
+class hytg_timed_launch(ctypes.Structure):
+    _fields_ = [("kind", u32), ("stream", u32), ("start_ms", dbl), ("end_ms", dbl), ("bytes", u64),
+                ("edges", u64), ("vertices", u64)]
+
+
+class hytg_serve_info(ctypes.Structure):
+    _fields_ = [("frames", u32), ("frames_free", u32), ("slots_per_frame", u32), ("pad_", u32),
+                ("frame_bytes", u64), ("edge_budget_bytes", u64), ("busy_slots", u64)]
 
 
 class hytg_cost_params(ctypes.Structure):
@@ -98,14 +110,17 @@ def load(path: Optional[str] = None):
             "hytg_plan": [vp, i32, vp, vp, vp, u32],
             "hytg_probe_link": [vp, u64, u32, P(dbl), P(dbl)],
             "hytg_get_iterations": [vp, vp, u32, P(u32)],
+            "hytg_get_timeline": [vp, vp, u32, P(u32)],
             "hytg_hub_order": [u64, vp, vp, dbl, vp, P(u64)],
             "hytg_get_permutation": [vp, vp, u64],
             "hytg_probe_atomics": [vp, u64, u32, P(dbl), P(dbl)],
+            "hytg_probe_atomics_hub": [vp, u64, u32, u32, P(dbl), P(dbl)],
             "hytg_serve_begin": [vp, i32, u32],
             "hytg_serve_admit": [vp, u32, u32],
             "hytg_serve_step": [vp, P(u64), P(u64)],
             "hytg_serve_fetch": [vp, u32, vp, u64],
             "hytg_serve_end": [vp],
+            "hytg_serve_get_info": [vp, P(hytg_serve_info)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -260,6 +275,12 @@ def hytg_probe_atomics(ctx, n: int = 1 << 28, reps: int = 5):
     return a.value, b.value
 
 
+def hytg_probe_atomics_hub(ctx, n: int = 1 << 28, reps: int = 5, n_rep: int = 4096):
+    a, b = dbl(), dbl()
+    _check(ctx, load().hytg_probe_atomics_hub(ctx, int(n), reps, n_rep, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def hytg_serve_begin(ctx, algo: int, n_slots: int):
     _check(ctx, load().hytg_serve_begin(ctx, int(algo), int(n_slots)))
 
@@ -280,6 +301,12 @@ def hytg_serve_fetch(ctx, slot: int, V: int, algo: int) -> np.ndarray:
     return out
 
 
+def hytg_serve_get_info(ctx) -> Dict:
+    s = hytg_serve_info()
+    _check(ctx, load().hytg_serve_get_info(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in hytg_serve_info._fields_ if name != "pad_"}
+
+
 def hytg_serve_end(ctx):
     _check(ctx, load().hytg_serve_end(ctx))
 
@@ -294,6 +321,20 @@ def hytg_get_iterations(ctx):
         out.append({name: (list(getattr(r, name)) if hasattr(getattr(r, name), "__len__")
                            else getattr(r, name)) for name, _ in hytg_iter_record._fields_})
     return out
+
+
+def hytg_get_timeline(ctx) -> np.ndarray:
+    """The last run's timed launches as a numpy structured array (fields of
+    hytg_timed_launch)."""
+    n = u32()
+    _check(ctx, load().hytg_get_timeline(ctx, None, 0, ctypes.byref(n)))
+    arr = (hytg_timed_launch * max(1, n.value))()
+    _check(ctx, load().hytg_get_timeline(ctx, arr, n.value, ctypes.byref(n)))
+    dt = np.dtype([("kind", np.uint32), ("stream", np.uint32), ("start_ms", np.float64),
+                   ("end_ms", np.float64), ("bytes", np.uint64), ("edges", np.uint64),
+                   ("vertices", np.uint64)])
+    assert dt.itemsize == ctypes.sizeof(hytg_timed_launch)
+    return np.frombuffer(bytes(arr), dtype=dt, count=n.value).copy()
 
 
 # ------------------------------------------------------------ convenience --
@@ -371,6 +412,9 @@ class Engine:
 
     def permutation(self) -> np.ndarray:
         return hytg_get_permutation(self.ctx, self.V)
+
+    def timeline(self) -> np.ndarray:
+        return hytg_get_timeline(self.ctx)
 
     def iterations(self):
         return hytg_get_iterations(self.ctx)

@@ -2,11 +2,13 @@
 
 One engine (hytg context with its own copy of the graph) per algorithm;
 each engine runs one batched run whose slots hold queries.  The loop admits
-arrived queries into free slots at iteration boundaries, steps every engine
-that has busy slots (one iteration each, interleaved, so the engines' device
-work overlaps), and retires converged queries.  Admission is bounded by the
-slots, i.e. by the per-query device state each engine holds (64 BFS/SSSP
-sources or 32 PPR seeds).
+arrived queries at iteration boundaries, steps every engine that has busy
+slots (one iteration each, interleaved, so the engines' device work
+overlaps), and retires converged queries.  Admission is by device memory:
+each engine's budget holds its edge-side data and its queries' state in
+frames of 8 queries, so a query is admitted only into a free slot whose
+group already has a frame, or whose group can take a free frame; otherwise
+it waits until a finished query gives memory back, even when slots are free.
 
 `python -m paper_2208_14935_gb300.serve` runs the serving benchmark on a
 synthetic graph and prints one JSON line.
@@ -47,6 +49,8 @@ class _Lane:
     occupant: List[Optional[Request]] = field(default_factory=list)
     waiting: collections.deque = field(default_factory=collections.deque)
     steps: int = 0
+    memory_waits: int = 0          # admissions refused for lack of a free frame
+    max_busy: int = 0              # most queries on the device at once
 
 
 class Server:
@@ -66,13 +70,39 @@ class Server:
             lane = _Lane(eng, algo, n, [None] * n)
             self.lanes[algo] = lane
 
+    FRAME = 8                      # slots [8 g, 8 g + 8) share one frame of device memory
+
     def _admit(self, lane: _Lane, t0: float, clock) -> None:
-        for s in range(lane.slots):
-            if lane.occupant[s] is None and lane.waiting:
-                r = lane.waiting.popleft()
+        """Free slots of groups that already hold a frame first (no new
+        memory), then slots of empty groups while the engine has a free frame."""
+        if not lane.waiting:
+            return
+        F = self.FRAME
+        groups = range((lane.slots + F - 1) // F)
+        framed = [any(lane.occupant[g * F:(g + 1) * F]) for g in groups]
+        order = ([s for g in groups if framed[g] for s in range(g * F, min((g + 1) * F, lane.slots))] +
+                 [s for g in groups if not framed[g] for s in range(g * F, min((g + 1) * F, lane.slots))])
+        memory_full = False
+        for s in order:
+            if not lane.waiting:
+                break
+            g = s // F
+            if lane.occupant[s] is not None or (memory_full and not framed[g]):
+                continue
+            r = lane.waiting[0]
+            try:
                 hytg.hytg_serve_admit(lane.eng.ctx, s, r.source)
-                r.admitted = clock() - t0
-                lane.occupant[s] = r
+            except hytg.HytgError as ex:
+                if ex.status != hytg.HYTG_ERR_BUDGET:
+                    raise
+                memory_full = True          # no free frame: the query waits for memory
+                lane.memory_waits += 1
+                continue
+            lane.waiting.popleft()
+            framed[g] = True
+            r.admitted = clock() - t0
+            lane.occupant[s] = r
+        lane.max_busy = max(lane.max_busy, sum(o is not None for o in lane.occupant))
 
     def _step(self, lane: _Lane, t0: float, clock) -> List[Request]:
         """One iteration of the lane's engine; returns the queries it finished."""
@@ -197,7 +227,10 @@ def _main():
     ap.add_argument("--graph", default="chunglu", choices=["chunglu", "rmat"])
     ap.add_argument("--log2v", type=int, default=26)
     ap.add_argument("--log2e", type=int, default=31)
-    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--budget-gb", type=float, default=16.0,
+                    help="device budget of the whole server (10^9 bytes), split among the engines")
+    ap.add_argument("--shares", default="0.29,0.29,0.42",
+                    help="fractions of the budget for the BFS, SSSP and PPR engines")
     ap.add_argument("--n", type=int, default=200, help="requests per rate")
     ap.add_argument("--rates", default="0.25,0.5,0.9", help="fractions of the saturation rate")
     ap.add_argument("--threads", action="store_true", help="one host thread per engine")
@@ -216,12 +249,18 @@ def _main():
         g = gg.rmat(args.log2v, edge_factor=1 << (args.log2e - args.log2v), seed=1)
     gen_s = time.perf_counter() - t
     budget = int(args.budget_gb * 1e9)
+    # the total budget is split among the three engines: each holds its own
+    # edge-side data and its queries' frames (8 queries each: BFS/SSSP V * 32
+    # bytes, PPR V * 96 bytes), so the split follows the frame sizes and the
+    # query mix (BFS:SSSP:PPR = 2:2:1)
+    shares = {a: float(x) for a, x in zip(("bfs", "sssp", "ppr"), args.shares.split(","))}
+    tot = sum(shares.values())
     engines = {}
     unweighted = gg.CSR(g.V, g.E, g.off, g.dst, None, g.name)
     for algo in ("bfs", "sssp", "ppr"):
         e = hytg.Engine(params={"part_bytes": 4 * 1024 * 1024})
         e.load(g if algo == "sssp" else unweighted)
-        e.set_budget(budget)
+        e.set_budget(int(budget * shares[algo] / tot))
         engines[algo] = e
     cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
     rng = np.random.default_rng(3)
@@ -232,9 +271,18 @@ def _main():
     srv.run(warm)
     sat_reqs = poisson_requests(args.n, float("inf"), pools, seed=10)
     sat = latency_stats(srv.run(sat_reqs))
+    mem = {}
+    for lane in srv.lanes.values():
+        hytg.hytg_serve_begin(lane.eng.ctx, hytg.ALGOS[lane.algo], lane.slots)
+        mem[lane.algo] = hytg.hytg_serve_get_info(lane.eng.ctx)
+        hytg.hytg_serve_end(lane.eng.ctx)
     out = {"metric": "served queries: p50/p99 latency and queries/s (continuous batching)",
            "graph": {"family": args.graph, "V": g.V, "E": g.E, "gen_s": round(gen_s, 1)},
            "budget_bytes": budget, "mix": "BFS:SSSP:PPR = 2:2:1", "slots": {"bfs": 64, "sssp": 64, "ppr": 32},
+           "engine_budget_bytes": {a: int(budget * shares[a] / tot) for a in shares},
+           "frames": {a: {"frames": m["frames"], "frame_bytes": m["frame_bytes"],
+                          "queries_at_once": m["frames"] * m["slots_per_frame"],
+                          "edge_budget_bytes": m["edge_budget_bytes"]} for a, m in mem.items()},
            "host_threads": 3 if args.threads else 1,
            "saturation": sat, "rates": {}}
     for frac in [float(x) for x in args.rates.split(",")]:
@@ -242,6 +290,8 @@ def _main():
         n = max(8, min(args.n, int(rate * args.max_seconds)))
         reqs = poisson_requests(n, rate, pools, seed=int(frac * 1000))
         out["rates"][f"{frac:g}x"] = {"offered_qps": rate, **latency_stats(srv.run(reqs))}
+    out["memory_waits"] = {a: l.memory_waits for a, l in srv.lanes.items()}
+    out["max_busy"] = {a: l.max_busy for a, l in srv.lanes.items()}
     print(json.dumps(out), flush=True)
     for e in engines.values():
         e.close()

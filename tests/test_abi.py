@@ -57,7 +57,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     import subprocess
     from paper_2208_14935_gb300 import hytg
     structs = {"hytg_stats": hytg.hytg_stats, "hytg_info": hytg.hytg_info,
-               "hytg_iter_record": hytg.hytg_iter_record, "hytg_cost_params": hytg.hytg_cost_params}
+               "hytg_iter_record": hytg.hytg_iter_record, "hytg_cost_params": hytg.hytg_cost_params,
+               "hytg_timed_launch": hytg.hytg_timed_launch, "hytg_serve_info": hytg.hytg_serve_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hytg.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')

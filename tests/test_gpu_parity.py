@@ -282,6 +282,46 @@ def test_budget_and_argument_errors(hy, rmat16):
     e.close()
 
 
+def test_cc_needs_symmetric_csr(hy, rmat16, rmat16_sym):
+    """CC is weakly connected components and needs a symmetric CSR: a directed
+    graph, or one whose reverse edges differ in multiplicity, is refused with
+    HYTG_ERR_ARG, and the context stays usable."""
+    e = engine(hy, rmat16, edge_bytes(rmat16, "cc") // 4)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("cc")
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    check(rmat16, "bfs", e.run("bfs", 0))
+    e.load(rmat16_sym)
+    check(rmat16_sym, "cc", e.run("cc"))
+    e.close()
+    g = gg.CSR(3, 4, np.array([0, 2, 3, 4], np.uint64), np.array([1, 1, 0, 2], np.uint32), None)
+    e = engine(hy, g, 1 << 20)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("cc")
+    assert ex.value.status == hy.HYTG_ERR_ARG
+    check(g, "bfs", e.run("bfs", 0))
+    e.close()
+
+
+def test_hostmem_failure_injected(hy, rmat16, monkeypatch):
+    """A pinned allocation that fails (made on the host by
+    HYTG_INJECT_HOSTMEM_FAIL) gives HYTG_ERR_HOSTMEM and leaves the context
+    usable: the next load and run succeed."""
+    e = hy.Engine(params={"part_bytes": 64 * 1024})
+    monkeypatch.setenv("HYTG_INJECT_HOSTMEM_FAIL", "1")
+    with pytest.raises(hy.HytgError) as ex:
+        e.load(rmat16)
+    assert ex.value.status == hy.HYTG_ERR_HOSTMEM
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("bfs", 0)
+    assert ex.value.status == hy.HYTG_ERR_STATE
+    monkeypatch.delenv("HYTG_INJECT_HOSTMEM_FAIL")
+    e.load(rmat16)
+    e.set_budget(edge_bytes(rmat16, "bfs") // 4)
+    check(rmat16, "bfs", e.run("bfs", 0))
+    e.close()
+
+
 def test_sssp_overflow(hy):
     g = gg.CSR(4, 3, np.array([0, 1, 2, 3, 3], np.uint64), np.array([1, 2, 3], np.uint32),
                np.array([0x7FFFFFFF, 0x7FFFFFFF, 5], np.uint32))

@@ -85,6 +85,56 @@ def test_cc_brute_force_tiny():
         assert orc.cc_bfs(s).tolist() == want
 
 
+def csr_from_edges(V, edges):
+    """CSR that keeps each row's edges in the given order (rows need not be sorted)."""
+    rows = [[] for _ in range(V)]
+    for u, v in edges:
+        rows[u].append(v)
+    off = np.zeros(V + 1, np.uint64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    dst = np.array([v for r in rows for v in r], dtype=np.uint32)
+    return gg.CSR(V, len(dst), off, dst, None, "hand")
+
+
+def brute_symmetric(g):
+    """The definition: the multiset of edges (u, v) equals the multiset of (v, u)."""
+    from collections import Counter
+    pairs = Counter((u, int(g.dst[e])) for u in range(g.V) for e in range(int(g.off[u]), int(g.off[u + 1])))
+    return all(pairs[(v, u)] == n for (u, v), n in pairs.items())
+
+
+# (V, edges, symmetric): each False case defeats one plausible shortcut; a
+# self-loop is its own reverse, so a graph of self-loops alone is symmetric.
+SYMMETRY_CASES = [
+    (3, [(0, 1), (1, 0), (1, 2)], False),                   # one reverse edge missing
+    (2, [(0, 1), (0, 1), (1, 0)], False),                   # unequal multiplicity
+    (3, [(0, 1), (1, 2), (2, 0)], False),                   # directed cycle: in-degree = out-degree everywhere
+    (4, [(0, 1), (1, 0), (2, 3), (3, 3), (3, 2), (2, 2)], True),
+    (3, [(0, 0), (2, 2), (2, 2)], True),                    # self-loops only
+    (3, [(1, 1), (1, 2)], False),                           # self-loop beside a missing reverse
+    (4, [(0, 3), (0, 1), (1, 0), (3, 0)], True),            # unsorted row, symmetric
+    (4, [(0, 3), (0, 1), (1, 0), (3, 1), (1, 3), (3, 0), (2, 1)], False),
+    (1, [], True),
+]
+
+
+@pytest.mark.parametrize("V,edges,want", SYMMETRY_CASES)
+def test_is_symmetric_hand_cases(V, edges, want):
+    g = csr_from_edges(V, edges)
+    assert brute_symmetric(g) == want
+    assert orc.is_symmetric(g) == want
+
+
+def test_is_symmetric_brute_force_tiny():
+    n_false = 0
+    for g in tiny_graphs(seed0=400):
+        want = brute_symmetric(g)
+        assert orc.is_symmetric(g) == want
+        n_false += not want
+        assert orc.is_symmetric(gg.symmetrize(g))
+    assert n_false > 20
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_alternates_agree_medium(seed):
     g = gg.random_graph(3000, 12000, seed=seed, skew=1.2, wmax=64)
