@@ -60,6 +60,10 @@ def parse():
                     help="comma-separated subset of bfs,sssp,cc,pagerank (profiling runs)")
     ap.add_argument("--no-probe", action="store_true", help="skip the host-link probe")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain runs")
+    ap.add_argument("--timeline-out", default="", metavar="PATH",
+                    help="save each algorithm's launch timeline of the last timed step (numpy .npz); "
+                         "with --param device_loop=0 its k_second_pass/k_relax entries follow the "
+                         "process's launch order, so a profiler's launch index maps to an edge count")
     ap.add_argument("--mesh-only", type=int, default=0, metavar="SIDE",
                     help="only the high-diameter workload: SIDE x SIDE 4-neighbour mesh with 0.1 %% "
                          "local shortcuts, weights in [1, 1000], 20 %% budget; BFS, SSSP, CC from "
@@ -453,9 +457,12 @@ def main():
             out = hytg.hytg_fetch_result(e.ctx, e.V, hytg.ALGOS[algo])
             wall = (time.perf_counter() - t0) * 1e3
             st = e.stats()
-            tl = timeline_summary(e.timeline(), hytg) if not args.no_timing else None
+            raw = e.timeline() if not args.no_timing else None
+            tl = timeline_summary(raw, hytg) if raw is not None else None
             per[algo] = {"stats": st, "wall_ms": wall, "d2h": out.nbytes,
                          "h2d": 0 if src is None else 4, "tl": tl}
+            if args.timeline_out:
+                per[algo]["tl_raw"] = raw
         return per
 
     # the link denominator, measured in this process before and after the timed steps
@@ -471,7 +478,13 @@ def main():
     probe_after = None if args.no_probe else eng.probe_link(1 << 30, 10)
     batched = None if args.no_batched else batched_vs_plain(hytg, eng, g)
     red_probe = None if args.no_probe else eng.probe_atomics(1 << 28, 5)
+    # the PageRank kernels' own target pattern: R-MAT in-degree skew after hub
+    # sorting, pushes to the first hub_replicas ids into per-SM replicas
+    hub_probe = None if args.no_probe else hytg.hytg_probe_atomics_hub(
+        eng.ctx, 1 << 28, 5, int(eng.get_param("hub_replicas")))
     probe = float("nan") if args.no_probe else (probe_before[0] + probe_after[0]) / 2
+    if args.timeline_out and rank == 0:
+        np.savez(args.timeline_out, **{a: steps[-1][a]["tl_raw"] for a in algos if "tl_raw" in steps[-1][a]})
 
     def tot(a, key, i=None):
         return sum((p[a]["stats"][key] if i is None else p[a]["stats"][key][i]) for p in steps)
@@ -541,36 +554,50 @@ def main():
             # per relaxed edge 4 B edge + 8 B value read-modify-write; per
             # scanned vertex 16 B offsets, 4 B delta read, 8 B delta and rank updates
             kern["k_second_pass<PageRank>"] = (sp_n, sp_ms, sp_e, sp_e * 12 + sp_v * 28,
-                                               "per edge 4 + 8 (value RMW), per scanned vertex 28")
+                                               "per edge 4 + 8 (value RMW), per scanned vertex 28",
+                                               sp_v)
         if rf_n:
             # per edge 4 B edge + 8 B RMW, per list entry 20 B
             kern["k_relax<PageRank> F route"] = (rf_n, rf_ms, rf_e, rf_e * 12 + rf_v * 20,
-                                                 "per edge 4 + 8 (value RMW), per active vertex 20")
+                                                 "per edge 4 + 8 (value RMW), per active vertex 20",
+                                                 rf_v)
         if kern:
             dom = max(kern, key=lambda k: kern[k][1])
-            n, ms, e_, alg, model = kern[dom]
+            n, ms, e_, alg, model, vv = kern[dom]
             achieved = alg / (ms * 1e-3) / 1e9
+            traffic, note = None, "no ncu DRAM capture of the current kernel"
+            if dom.startswith("k_second_pass"):
+                # DRAM bytes from one cold-cache ncu capture of each of its two
+                # launches on R-MAT 22: the push read 29.8 MB for 4,183,639
+                # edges, the take 0.43 MB for 22,240 vertices; scaled to this
+                # run's mean launch by its edges and vertices
+                traffic = (29.778176e6 / 4183639) * (e_ / n) + (430592.0 / 22240) * (vv / n)
+                note = ("scaled from ncu captures on R-MAT 22 (push 7.12 B/edge, take 19.4 B/vertex, "
+                        "cold cache) by this run's edges and vertices per launch")
             roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved / hbm, "traffic": None,
-                        "traffic_note": "no ncu DRAM capture of the current kernel",
+                        "frac": achieved / hbm, "traffic": traffic, "traffic_note": note,
                         "bytes_model": model, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                         "launches": n, "avg_launch_us": ms * 1e3 / n, "alg_bytes_per_launch": alg / n,
                         "edges_per_launch": e_ / n,
                         "binding_roof": "L2 reductions (roofline_l2): the value arrays stay in L2"}
-            if red_probe:
+            if red_probe and hub_probe:
                 roofline_l2 = {}
-                for k, (n, ms, e_, _, _) in kern.items():
+                peak = hub_probe[1]
+                for k, (n, ms, e_, _, _, _) in kern.items():
                     rate = e_ / (ms * 1e-3) / 1e9
-                    roofline_l2[k] = {"bound": "l2_reductions", "achieved": rate, "peak": red_probe[0],
-                                      "unit": "G updates/s", "frac": rate / red_probe[0],
-                                      "frac_of_skewed_probe": rate / red_probe[1]}
-                roofline_l2["peak_source"] = ("hytg_probe_atomics in this run: uniform targets (peak), "
-                                              "R-MAT-skewed targets")
+                    roofline_l2[k] = {"bound": "l2_reductions", "achieved": rate, "peak": peak,
+                                      "unit": "G updates/s", "frac": rate / peak,
+                                      "frac_of_uniform_probe": rate / red_probe[0]}
+                roofline_l2["peak_source"] = ("hytg_probe_atomics_hub in this run: the R-MAT in-degree "
+                                              "skew after hub sorting, with the kernels' per-SM replicas")
+                roofline_l2["uniform_gops"] = red_probe[0]
                 roofline_l2["skewed_gops"] = red_probe[1]
+                roofline_l2["hub_skew_without_replicas_gops"] = hub_probe[0]
                 # all PageRank reductions over its device time (kernels overlap on 5 streams)
                 pr_e = sum(st["edges_relaxed"] + st["extra_edges"] for st in prs)
                 pr_ms = sum(st["device_ms"] for st in prs)
                 roofline_l2["pagerank_aggregate_gops"] = pr_e / (pr_ms * 1e-3) / 1e9
+                roofline_l2["pagerank_aggregate_frac"] = pr_e / (pr_ms * 1e-3) / 1e9 / peak
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

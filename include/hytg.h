@@ -176,7 +176,7 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * RTT_zc, stored as multiples of 1e-6), "m" (request bytes), "MR" (outstanding
  * requests), "k" (partitions per F task, Sec. V-B), "part_bytes" (partition
  * size in bytes of 4-byte entries, Sec. V-B), "streams" (F compute streams),
- * "prefetch_slots" (staging slots beyond one per F stream, default 2: each
+ * "prefetch_slots" (staging slots beyond one per F stream, default 4: each
  * slot has its own copy stream, so later tasks' copies run while earlier
  * tasks still hold their slots),
  * "staging_frac", "compact_frac" (shares of the budget), "force_route"
@@ -200,15 +200,29 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * PageRank/PPR iteration in decreasing order of the pending |delta| their
  * partitions hold, 0 in partition order; other algorithms always use
  * partition order, which hub sorting makes hub-first), "device_loop" (1,
- * default: single-source runs replay one iteration (planning, binning,
- * cache and zero-copy relax) inside a CUDA graph with a WHILE node until an
- * iteration needs the F or C route, whose copies the host issues, or the
- * run ends; 0: the host drives every iteration.  Iterations run in the
- * graph report no per-iteration device time and are not in kernel_ms; if
- * the installed CUDA driver cannot build the graph, the context keeps using
- * the host loop and graph_launches stays 0), "serve_frames" (serving:
+ * default: runs replay one iteration (planning, binning, cache and zero-copy
+ * relax) inside a CUDA graph with a WHILE node; a single-source iteration
+ * that needs the F or C route goes to the host, which issues its copies,
+ * while batched runs keep F and C iterations in the graph too: one IF node
+ * per partition copies it into a staging slot and relaxes it, one IF node
+ * gathers and relaxes the C route, each F copy moves one partition (no task
+ * combination, partition order), and only a C route larger than the
+ * compaction buffer goes to the host; 2: single-source runs keep F and C
+ * iterations in the graph as well; 0: the host drives every iteration.
+ * Iterations run in the graph report no per-iteration device time and are
+ * not in kernel_ms or the timeline; if the installed CUDA driver cannot build
+ * the graph, the context keeps using the host loop and graph_launches stays
+ * 0 (and if it cannot hold the F and C nodes, those iterations go to the
+ * host as at 1), "serve_frames" (serving:
  * cap on the query frames hytg_serve_begin plans, 0 (default): as many as
- * the slots can use; see hytg_serve_get_info).
+ * the slots can use; see hytg_serve_get_info), "batch_sparse_below" (batched
+ * SSSP/PPR relax: a warp whose 32 edges carry fewer active sources per edge
+ * than this on average walks the sources of each lane's own edge; otherwise
+ * it walks its edges with a lane per source; 0 never, 65 always; -1
+ * (default): 16 for SSSP, always for PPR, the best of a sweep on R-MAT 24),
+ * "host_huge" (1, default: hytg_load_csr places the edge arrays in
+ * anonymous memory advised for transparent huge pages and registers it with
+ * the driver, falling back to cudaHostAlloc if that fails; 0: cudaHostAlloc).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);
@@ -330,6 +344,9 @@ typedef struct hytg_timed_launch {
                                          more than 16,382 second passes ran and the later ones
                                          share a counter) */
     uint64_t vertices;                /* HYTG_K_SECOND_PASS: vertices of the range it scanned */
+    uint32_t part_first, part_last;   /* HYTG_K_COPY_F, HYTG_K_RELAX_F, HYTG_K_SECOND_PASS of an F
+                                         task: the task's partitions [part_first, part_last]
+                                         (task combination, Sec. V-B); else 0, 0 */
 } hytg_timed_launch;
 hytg_status hytg_get_timeline(hytg_ctx *ctx, hytg_timed_launch *out, uint32_t cap, uint32_t *n);
 

@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListA
                                                              const Summary *sum, RelaxTask t) {
     __shared__ TileSmem<true> sm;
     if (b.loop && !b.loop->work) return;
-    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
-    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    unsigned long long kb, ke;
+    task_range(t, sum, kb, ke);
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListA
 // source (SSSP: s = lane and lane + 32; PPR: s = lane), reading each
 // source's value row in one sector per frame; otherwise every lane keeps its
 // own edge and loops over the sources active at its u, so that 32 edges'
-// loads are in flight together instead of one edge's.
+// loads are in flight together instead of one edge's (the switch point is
+// the "batch_sparse_below" parameter).
 template <int MODE>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, ListArrays la,
                                                               const Summary *sum, RelaxTask t,
@@ -257,8 +258,8 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                                                               unsigned int *overflow) {
     __shared__ TileSmem<true> sm;
     if (b.loop && !b.loop->work) return;
-    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
-    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    unsigned long long kb, ke;
+    task_range(t, sum, kb, ke);
     if (kb >= ke) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
             unsigned int pop = __popcll(fj);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
-            if (pop < 8u * 32u) {
+            if (pop < b.sparse_below * 32u) {
                 // sparse masks: a lane per edge, looping over its active sources
                 if (MODE == kBatchSSSP) {
                     unsigned long long m = fj, imp = 0;
@@ -423,7 +424,7 @@ cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, cons
                                  const RelaxTask &t, int grid_cap, unsigned int *bm,
                                  unsigned int *overflow, cudaStream_t s) {
     unsigned int grid = (unsigned int)grid_cap;
-    if (!t.device_sized) {
+    if (!t.device_sized && !t.dev_edge) {
         if (t.k_begin >= t.k_end) return cudaSuccess;
         const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
         if (tiles < grid) grid = (unsigned int)tiles;

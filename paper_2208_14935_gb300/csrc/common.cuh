@@ -144,9 +144,19 @@ struct LoopCtl {
     unsigned long long max_it;
     unsigned long long m;           // request bytes (link bytes of zero-copy lines)
     void *rec;                      // hytg_iter_record[rec_cap]
+    // F and C iterations inside the loop ("device_loop" 2): the IF-node
+    // handle of every partition's F task (nullptr: F iterations go to the
+    // host) and of the C route (0: C iterations go to the host)
+    const unsigned long long *f_handles;
+    unsigned long long c_handle;
+    unsigned long long c_cap;       // compaction buffer, in edges (larger C routes go to the host)
+    const unsigned char *route;     // per-partition routes of the iteration
+    const unsigned long long *part_eb;
+    unsigned int n_parts, n_arrays;
     // totals over the device iterations of this launch
     unsigned long long route_parts[kRoutes], route_entries[kRoutes], route_edges[kRoutes];
     unsigned long long z_lines, vertices, edges, iterations;
+    unsigned long long f_parts, f_bytes, c_iters, c_lines;
 };
 
 struct AlgoState {
@@ -192,6 +202,9 @@ struct BatchState {
     unsigned int *fr32;                   // PPR seeds taken at v this iteration
     unsigned long long *alive;            // OR of every vertex's frontier mask (serving)
     const LoopCtl *loop;                  // device loop: level from loop->it; relax gated by loop->work
+    unsigned int sparse_below;            // SSSP/PPR relax: a warp whose 32 edges carry fewer than
+                                          // this many active sources per edge on average loops
+                                          // over sources per lane (0: never)
 };
 __device__ __forceinline__ unsigned int *bval(const BatchState &b, unsigned long long v, unsigned int s) {
     return b.val[s >> 3] + v * kFrameSources + (s & 7);
@@ -229,6 +242,10 @@ struct RelaxTask {
     unsigned long long src_len;         // valid indices of dst / w: [0, src_len)
     unsigned long long *link_ctr;       // host-memory reads (Z relax, C gather): {32-byte
                                         // sectors, 128-byte lines} read, or nullptr
+    // One partition's F task inside the device loop: its first edge in the F
+    // route's edge space, its active edges and its first list entry, read on
+    // the device where k_select and k_bin left them (nullptr: host bounds)
+    const unsigned long long *dev_edge, *dev_len, *dev_entry;
 };
 
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
@@ -254,7 +271,7 @@ cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *of
                                unsigned int *err, cudaStream_t s);
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
-                          cudaStream_t s);
+                          cudaStream_t s, const LoopCtl *loop = nullptr);
 
 cudaError_t launch_b_init(const BatchState &b, unsigned long long V, unsigned long long n_words_alloc,
                           const unsigned int *src_dev, unsigned int K, float base, unsigned int *bm,
@@ -279,6 +296,12 @@ cudaError_t launch_b_finalize(const BatchState &b, unsigned long long V, unsigne
                               const unsigned int *perm, void *out, double *sums, cudaStream_t s);
 
 cudaError_t launch_zero_u64(unsigned long long *p, unsigned long long n, cudaStream_t s);
+// Copy n 4-byte words from mapped host memory to device memory with 16-byte
+// loads (the device loop's F copy where a memcpy node cannot be used);
+// gated by loop->work.  Both addresses 16-byte aligned, n a multiple of 4
+// except for the tail, which is copied word by word.
+cudaError_t launch_copy_words(const unsigned int *src, unsigned int *dst, unsigned long long n,
+                              const LoopCtl *loop, cudaStream_t s);
 cudaError_t launch_loop_decide(const Summary *sum, LoopCtl *ctl, unsigned long long cond_handle,
                                cudaStream_t s);
 

@@ -15,6 +15,8 @@
 //      task), the C route on another stream, cache and Z on the main stream.
 // The next iteration's planning kernels wait, on the device, for every
 // stream of the previous one, so the host only blocks on the summary copy.
+#include <sys/mman.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -52,6 +54,7 @@ struct TimedLaunch {
     int stream;                 // 0 main, 1 compaction, 2 + i F stream i
     uint64_t bytes, edges, vertices;
     int sp_slot;                // second pass: its counter slot, else -1
+    uint32_t part_first, part_last;
 };
 
 // One F task after combination: partitions [i, j], their edges, and the
@@ -148,6 +151,8 @@ struct hytg_ctx {
     uint64_t V = 0, E = 0;
     bool weighted = false;
     uint32_t *h_dst = nullptr, *h_w = nullptr;          // pinned, mapped
+    size_t h_map_bytes[2] = {};                          // "host_huge": mmap'd length of h_dst / h_w (0: cudaHostAlloc)
+    void *h_map_base[2] = {};
     const uint32_t *m_dst = nullptr, *m_w = nullptr;    // device view of the same memory
     std::vector<uint64_t> h_off;                         // row offsets in internal ids
     // hub sorting (Sec. VI-A): internal id n holds original vertex perm[n]
@@ -231,7 +236,7 @@ struct hytg_ctx {
     double alpha = 0.8, beta = 0.4, gamma = 0.625, m = 128, MR = 256, k = 4;
     double part_bytes = 4.0 * 1024 * 1024;
     double streams = 4, staging_frac = 0.5, compact_frac = 0.05;
-    double prefetch_slots = 2;                           // staging slots beyond one per F stream
+    double prefetch_slots = 4;                           // staging slots beyond one per F stream
     double force_route = -1, seed = 1, pr_damping = 0.85, pr_eps = 1e-9, max_iters = 1e8;
     double timing = 0;
     double hub_frac = 0.08;                              // Sec. VI-A: top 8 % of vertices
@@ -241,7 +246,10 @@ struct hytg_ctx {
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
+    double host_huge = 1;                                // edge arrays in transparent huge pages, registered
     double serve_frames_param = 0;                       // serving: cap on query frames (0: what the slots need)
+    double batch_sparse_below = -1;                      // batched SSSP/PPR relax path switch (sources per
+                                                         // edge); -1: 16 for SSSP, always for PPR
     uint64_t auto_delta = 0;                             // auto bucket width from the weights
 
     // last run
@@ -267,6 +275,17 @@ struct hytg_ctx {
     // device-driven iteration loop: a graph whose WHILE node repeats one
     // iteration (plan, k_loop_decide, bin, cache and Z relax) on the device
     cudaStream_t s_cap = nullptr;                        // capture stream
+    cudaStream_t s_cap2 = nullptr;                       // capture stream of the IF-node bodies
+    // F and C iterations inside the loop: IF-node handles (host copy, device
+    // array), the C route's node, kernels per F / C body, how F copies run
+    std::vector<unsigned long long> loop_fh;
+    unsigned long long *d_loop_fh = nullptr;
+    unsigned long long loop_ch = 0;
+    uint32_t loop_f_kernels = 0, loop_c_kernels = 0;
+    bool loop_fc = false;                                // the captured body holds F and C nodes
+    int last_run_arrays = 1;                             // edge arrays the current run reads
+    int loop_fc_copy = 0;                                // 0 memcpy nodes, 1 copy kernel, 2 not available
+
     cudaGraph_t loop_graph = nullptr;
     cudaGraphExec_t loop_exec = nullptr;
     std::string loop_key;                                // what the captured body depends on
@@ -311,10 +330,67 @@ void free_loop_graph(hytg_ctx *c) {
     c->loop_key.clear();
 }
 
+void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &fn);
+
+hytg_status alloc_edge_array_huge(hytg_ctx *c, int a, uint32_t **out, size_t bytes);
+
+// Pinned, device-mapped host memory for edge array a (0 dst, 1 weights).
+// With "host_huge" (default) an anonymous mapping advised for transparent
+// huge pages, aligned to 512 MiB (the huge-page size of a 64 KiB base-page
+// kernel; a 2 MiB one divides it) and registered with the driver, so that
+// the GPU's accesses over the link need far fewer page translations (runs
+// that alternate between contexts' arrays no longer slow down at random);
+// cudaHostAlloc if that fails or "host_huge" is 0.
+hytg_status alloc_edge_array(hytg_ctx *c, int a, uint32_t **out, size_t bytes) {
+    *out = nullptr;
+    if (c->host_huge != 0 && alloc_edge_array_huge(c, a, out, bytes) == HYTG_OK) return HYTG_OK;
+    if (cudaHostAlloc((void **)out, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return HYTG_ERR_HOSTMEM;
+    }
+    return HYTG_OK;
+}
+
+hytg_status alloc_edge_array_huge(hytg_ctx *c, int a, uint32_t **out, size_t bytes) {
+    const size_t align = size_t(512) << 20;
+    const size_t len = (bytes + align - 1) / align * align + align;
+    void *base = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (base == MAP_FAILED) return HYTG_ERR_HOSTMEM;
+    char *p = (char *)(((uintptr_t)base + align - 1) & ~(uintptr_t)(align - 1));
+    madvise(p, bytes, MADV_HUGEPAGE);
+    // touch every page so that it is faulted in (as a huge page where the
+    // kernel can) before the driver pins it
+    parallel_chunks(bytes / 4096, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t i = lo; i < hi; ++i) p[i * 4096] = 0;
+    });
+    if (cudaHostRegister(p, bytes, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
+        cudaGetLastError();
+        munmap(base, len);
+        return HYTG_ERR_HOSTMEM;
+    }
+    c->h_map_base[a] = base;
+    c->h_map_bytes[a] = len;
+    *out = (uint32_t *)p;
+    return HYTG_OK;
+}
+
+void free_edge_array(hytg_ctx *c, int a, uint32_t *p) {
+    if (!p) return;
+    if (c->h_map_bytes[a]) {
+        cudaHostUnregister(p);
+        munmap(c->h_map_base[a], c->h_map_bytes[a]);
+        c->h_map_bytes[a] = 0;
+        c->h_map_base[a] = nullptr;
+    } else {
+        cudaFreeHost(p);
+    }
+}
+
 void free_graph(hytg_ctx *c) {
     free_loop_graph(c);             // its body holds pointers into the graph's arrays
-    if (c->h_dst) cudaFreeHost(c->h_dst);
-    if (c->h_w) cudaFreeHost(c->h_w);
+    free_edge_array(c, 0, c->h_dst);
+    free_edge_array(c, 1, c->h_w);
     c->h_dst = c->h_w = nullptr;
     c->m_dst = c->m_w = nullptr;
     dfree(c->d_off); dfree(c->d_val); dfree(c->d_delta); dfree(c->d_bm[0]); dfree(c->d_bm[1]);
@@ -624,6 +700,7 @@ struct ScopedTime {
     cudaEvent_t a = nullptr;
     uint64_t bytes = 0, edges = 0, vertices = 0;
     int sp_slot = -1;
+    uint32_t part_first = 0, part_last = 0;
     ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_, bool kernel = true) : c(c_), kind(kind_), s(s_) {
         const unsigned k = (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
         if (c->capturing) {              // inside a graph body: counted per body run
@@ -640,7 +717,8 @@ struct ScopedTime {
         if (a) {
             cudaEvent_t b = pool_event(c);
             cudaEventRecord(b, s);
-            c->timed.push_back({kind, a, b, stream_index(c, s), bytes, edges, vertices, sp_slot});
+            c->timed.push_back({kind, a, b, stream_index(c, s), bytes, edges, vertices, sp_slot, part_first,
+                                part_last});
         }
     }
 };
@@ -737,6 +815,12 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
     return st;
 }
 
+// Initial residual of a PPR seed: (1 - d) V, the total that PageRank starts
+// with, so that the FP32 threshold eps bounds the same relative error (with
+// 1 - d at the seed alone, eps = 1e-9 left an L1 error near 0.1 on 2^24
+// vertices).  Results are normalised, so the scale cancels.
+float ppr_seed_mass(const hytg_ctx *c) { return (float)((1.0 - c->pr_damping) * (double)c->V); }
+
 // "two_pass": 0 off, 1 PageRank/PPR only (default), 2 every algorithm.
 bool second_pass_on(const hytg_ctx *c, int algo) {
     if (c->batch_mode != kBatchNone || c->two_pass == 0) return false;
@@ -789,6 +873,8 @@ hytg_status ensure_batch(hytg_ctx *c, int mode, uint32_t out_rows) {
     }
     c->bs.mode = mode;
     c->bs.alive = c->d_alive;
+    c->bs.sparse_below = c->batch_sparse_below >= 0 ? (unsigned int)c->batch_sparse_below
+                                                    : (mode == kBatchPPR ? 65u : 16u);
     for (auto &p : c->bs.val) p = nullptr;
     for (uint32_t g = 0; g < kMaxPprFrames; ++g) c->bs.delta[g] = c->bs.rank[g] = c->bs.msg[g] = nullptr;
     return HYTG_OK;
@@ -833,7 +919,8 @@ hytg_status attach_own_frames(hytg_ctx *c, int mode, uint32_t K) {
     return HYTG_OK;
 }
 
-hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop);
+hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop,
+                            int part = 0);
 
 // Start mark of the next iteration record (timing on).
 void iteration_mark(hytg_ctx *c) {
@@ -886,15 +973,21 @@ hytg_status issue_plan(hytg_ctx *c, int algo, unsigned int bucket, uint32_t it, 
 // then the cache relax (and its second pass) and the zero-copy relax.
 // `loop` is set when the launches are captured into the device loop's body:
 // they then run only if k_loop_decide gave the iteration to the device.
-hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop) {
+// part: 0 everything; while capturing the device loop's body, 1 stops after
+// k_bin and 2 issues only what follows it.
+hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStream_t s, LoopCtl *loop,
+                            int part) {
     GraphDev g = graph_dev(c);
     AlgoState st = algo_state(c, algo, bucket);
     st.loop = loop;
     PartArrays pa = part_arrays(c);
     ListArrays la = list_arrays(c);
     Summary *sum = (Summary *)c->d_sumbuf;
-    { ScopedTime t(c, HYTG_K_BIN, s); CK(launch_bin(g, st, pa, la, sum, s)); }
-    if (!c->capturing) CK(cudaEventRecord(c->ev_bin, s));
+    if (part != 2) {
+        { ScopedTime t(c, HYTG_K_BIN, s); CK(launch_bin(g, st, pa, la, sum, s)); }
+        if (!c->capturing) CK(cudaEventRecord(c->ev_bin, s));
+    }
+    if (part == 1) return HYTG_OK;
     const int cap = 4 * (int)device_sms();
     if (c->capturing && c->batch_mode == kBatchNone && c->carve.n_cached > 0) {
         // device loop body: cache and zero-copy routes in one launch
@@ -952,6 +1045,133 @@ bool loop_applies(const hytg_ctx *c) {
     return c->device_loop != 0 && c->force_route != 5 && !c->serving;
 }
 
+// F and C iterations can stay in the device loop: batched runs at "device_loop"
+// 1, every run at 2; not with host compaction, forced random routes, more
+// partitions than 1024 IF nodes, or a staging slot without room for one
+// partition (plus 3 words of alignment slack when the copy kernel, not a
+// memcpy node, moves it).
+bool loop_fc_wanted(const hytg_ctx *c) {
+    if (c->device_loop < 2 && c->batch_mode == kBatchNone) return false;
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    const uint64_t slack = c->loop_fc_copy == 1 ? 3 : 0;
+    return c->compact_host == 0 && c->force_route != 5 && N >= 1 && N <= 1024 && c->carve.n_slots >= 1 &&
+           c->carve.slot_edges >= c->max_part_edges + slack;
+}
+
+// One IF node per partition (copy the partition into the staging slot of its
+// lane, relax it, and for PageRank/PPR its second pass), chained per slot so
+// that a slot's next user starts after the previous one; one IF node for the
+// C route (gather into the compaction buffer, relax).  k_loop_decide opens the
+// nodes of the partitions it routed F and the C node when C fits the buffer.
+hytg_status capture_loop_fc(hytg_ctx *c, int algo, cudaGraph_t cg, const std::vector<cudaGraphNode_t> &after_bin) {
+    const uint32_t N = (uint32_t)(c->part_vb.size() - 1);
+    Carve &cv = c->carve;
+    const int n_arrays = (algo == kSSSP) ? 2 : 1;
+    AlgoState st = algo_state(c, algo);
+    st.loop = c->d_loop;
+    PartArrays pa = part_arrays(c);
+    ListArrays la = list_arrays(c);
+    Summary *sum = (Summary *)c->d_sumbuf;
+    const int cap = 8 * (int)device_sms();
+    if (!c->d_loop_fh) return fail(c, HYTG_ERR_CUDA, "device loop: no handle array");
+    c->loop_fh.assign(N, 0);
+    const uint32_t S = cv.n_slots;
+    std::vector<cudaGraphNode_t> lane(S, nullptr);
+    auto add_if = [&](const std::vector<cudaGraphNode_t> &d, cudaGraphConditionalHandle *h, cudaGraphNode_t *node,
+                      cudaGraph_t *body) -> cudaError_t {
+        cudaError_t e = cudaGraphConditionalHandleCreate(h, cg, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return e;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = *h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(node, cg, d.data(), nullptr, d.size(), &np);
+        if (e == cudaSuccess) *body = np.conditional.phGraph_out[0];
+        return e;
+    };
+    const uint32_t k_before = c->loop_kernels;
+    c->loop_f_kernels = 0;
+    for (uint32_t i = 0; i < N; ++i) {
+        const uint32_t k_node = c->loop_kernels;
+        const uint32_t L = i % S;
+        std::vector<cudaGraphNode_t> d = lane[L] ? std::vector<cudaGraphNode_t>{lane[L]} : after_bin;
+        cudaGraphConditionalHandle h;
+        cudaGraphNode_t node;
+        cudaGraph_t body;
+        CK(add_if(d, &h, &node, &body));
+        c->loop_fh[i] = (unsigned long long)h;
+        lane[L] = node;
+        const uint64_t eb = c->part_eb[i], ee = c->part_eb[i + 1];
+        // the copy kernel reads from the 16-byte boundary at or below the
+        // partition's first edge; a memcpy node copies the partition exactly
+        const uint64_t e0 = c->loop_fc_copy == 1 ? (eb & ~uint64_t(3)) : eb;
+        CK(cudaStreamBeginCaptureToGraph(c->s_cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        hytg_status r = HYTG_OK;
+        cudaError_t e = cudaSuccess;
+        if (ee > eb) {
+            if (c->loop_fc_copy == 0) {
+                e = cudaMemcpyAsync(cv.slot_dst[L], c->h_dst + eb, (ee - eb) * 4, cudaMemcpyHostToDevice, c->s_cap2);
+                if (e == cudaSuccess && n_arrays == 2)
+                    e = cudaMemcpyAsync(cv.slot_w[L], c->h_w + eb, (ee - eb) * 4, cudaMemcpyHostToDevice, c->s_cap2);
+            } else {
+                e = launch_copy_words(c->m_dst + e0, cv.slot_dst[L], ee - e0, c->d_loop, c->s_cap2);
+                if (e == cudaSuccess && n_arrays == 2)
+                    e = launch_copy_words(c->m_w + e0, cv.slot_w[L], ee - e0, c->d_loop, c->s_cap2);
+                c->loop_kernels += n_arrays;
+            }
+            RelaxTask t{};
+            t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[L]; t.w = cv.slot_w[L];
+            t.shift = (long long)e0; t.src_len = ee - e0;
+            t.dev_edge = pa.route_edge + i; t.dev_len = pa.edges + i; t.dev_entry = pa.route_entry + i;
+            if (e == cudaSuccess) {
+                ScopedTime tm(c, HYTG_K_RELAX_F, c->s_cap2);
+                e = relax_any(c, st, la, sum, t, cap, c->s_cap2);
+            }
+            if (e == cudaSuccess && second_pass_on(c, algo)) {
+                ScopedTime tm(c, kKindSecondPass, c->s_cap2);
+                e = launch_second_pass(st, c->d_off, cv.slot_dst[L], cv.slot_w[L], (long long)e0, ee - e0,
+                                       c->part_vb[i], c->part_vb[i + 1], eb, ee, sp_scratch(c), c->d_sp,
+                                       c->d_err, c->s_cap2);
+                count_second_launch(c);
+            }
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(c->s_cap2, &captured);
+        if (e != cudaSuccess) r = fail(c, HYTG_ERR_CUDA, std::string("F node of the device loop: ") + cudaGetErrorString(e));
+        else if (e_end != cudaSuccess)
+            r = fail(c, HYTG_ERR_CUDA, std::string("F node capture: ") + cudaGetErrorString(e_end));
+        if (r != HYTG_OK) return r;
+        if (c->loop_kernels > k_node && c->loop_f_kernels == 0) c->loop_f_kernels = c->loop_kernels - k_node;
+    }
+    c->loop_kernels = k_before;              // F-node kernels are counted per opened node
+    {
+        // the C route in one chunk of the compaction buffer
+        cudaGraphConditionalHandle h;
+        cudaGraphNode_t node;
+        cudaGraph_t body;
+        CK(add_if(after_bin, &h, &node, &body));
+        c->loop_ch = (unsigned long long)h;
+        CK(cudaStreamBeginCaptureToGraph(c->s_cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        RelaxTask gt{};
+        gt.route = kRouteC; gt.mode = kModeHost; gt.dst = c->m_dst; gt.w = c->m_w; gt.shift = 0;
+        gt.device_sized = true; gt.src_len = c->E; gt.link_ctr = c->d_link_ctr + 2 * kRouteC;
+        cudaError_t e = launch_gather(la, sum, gt, cv.cmp_dst, n_arrays == 2 ? cv.cmp_w : nullptr, cap, c->s_cap2,
+                                      c->d_loop);
+        RelaxTask rt{};
+        rt.route = kRouteC; rt.mode = kModeCompact; rt.dst = cv.cmp_dst; rt.w = cv.cmp_w; rt.shift = 0;
+        rt.device_sized = true; rt.src_len = cv.compact_edges;
+        if (e == cudaSuccess) e = relax_any(c, st, la, sum, rt, cap, c->s_cap2);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(c->s_cap2, &captured);
+        if (e != cudaSuccess || e_end != cudaSuccess)
+            return fail(c, HYTG_ERR_CUDA, std::string("C node of the device loop: ") +
+                                              cudaGetErrorString(e != cudaSuccess ? e : e_end));
+        c->loop_c_kernels = 2;
+    }
+    return HYTG_OK;
+}
+
 hytg_status capture_loop_body(hytg_ctx *c, int algo, cudaStream_t s, unsigned long long handle) {
     GraphDev g = graph_dev(c);
     AlgoState st = algo_state(c, algo);
@@ -985,17 +1205,24 @@ hytg_status capture_loop_body(hytg_ctx *c, int algo, cudaStream_t s, unsigned lo
     { ScopedTime t(c, HYTG_K_COUNT, s); CK(launch_count(g, st, pa, (unsigned long long)c->m, s)); }
     { ScopedTime t(c, HYTG_K_COUNT, s); CK(launch_select(g, pa, cost_params(c, algo, 1), sum, s)); }
     { ScopedTime t(c, HYTG_K_OTHER, s); CK(launch_loop_decide(sum, c->d_loop, handle, s)); }
-    return issue_plan_tail(c, algo, 0xFFFFFFFFu, s, c->d_loop);
+    return issue_plan_tail(c, algo, 0xFFFFFFFFu, s, c->d_loop, 1);
 }
 
 hytg_status ensure_loop_graph(hytg_ctx *c, int algo) {
     char key[512];
-    std::snprintf(key, sizeof key, "%d|%d|%u|%p|%u|%llu|%d|%p|%u|%p|%p|%p|%g|%g|%g|%g|%g|%g|%g|%g|%g|%llu|%zu|%g",
+    std::snprintf(key, sizeof key, "%d|%d|%u|%p|%u|%llu|%d|%p|%u|%p|%p|%p|%g|%g|%g|%g|%g|%g|%g|%g|%g|%llu|%zu|%g|%g|%p",
                   algo, c->batch_mode, c->batch_K, (void *)c->carve.cache_dst, c->carve.n_cached,
                   (unsigned long long)c->carve.cache_edges, (int)second_pass_on(c, algo), (void *)c->d_hub_rep,
                   c->n_hub_rep, (void *)c->d_sumbuf, (void *)c->d_val, (void *)c->d_ebase, c->alpha, c->beta,
                   c->gamma, c->m, c->MR, c->force_route, c->pr_damping, c->pr_eps, c->priority,
-                  (unsigned long long)c->n_words_alloc, c->part_vb.size(), c->hub_frac);
+                  (unsigned long long)c->n_words_alloc, c->part_vb.size(), c->hub_frac, c->batch_sparse_below,
+                  (void *)c->bs.val[0]);
+    {
+        const size_t n = std::strlen(key);
+        std::snprintf(key + n, sizeof key - n, "|fc%d.%d|%u|%p|%p|%llu", (int)c->loop_fc, c->loop_fc_copy,
+                      c->carve.n_slots, (void *)c->carve.slot_dst[0], (void *)c->carve.cmp_dst,
+                      (unsigned long long)c->carve.compact_edges);
+    }
     if (c->loop_exec && c->loop_key == key) return HYTG_OK;
     free_loop_graph(c);
     cudaGraph_t g = nullptr;
@@ -1011,17 +1238,41 @@ hytg_status ensure_loop_graph(hytg_ctx *c, int algo) {
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(c->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    c->capturing = true;
+    // The body is captured in two pieces that meet at k_bin: planning up to
+    // k_bin, then (from k_bin's node) the cache and zero-copy relaxes; the F
+    // and C IF nodes are added to the finished body, also after k_bin, and
+    // each IF node's own body is captured on the second capture stream.
     c->loop_kernels = 0;
-    hytg_status st = capture_loop_body(c, algo, c->s_cap, (unsigned long long)h);
-    c->capturing = false;
-    cudaGraph_t captured = nullptr;
-    const cudaError_t e_end = cudaStreamEndCapture(c->s_cap, &captured);
-    if (st != HYTG_OK) { free_loop_graph(c); return st; }
-    if (e_end != cudaSuccess) {
-        free_loop_graph(c);
-        return fail(c, HYTG_ERR_CUDA, std::string("capture of the device loop: ") + cudaGetErrorString(e_end));
+    std::vector<cudaGraphNode_t> after_bin;
+    for (int piece = 0; piece < 2; ++piece) {
+        CK(cudaStreamBeginCaptureToGraph(c->s_cap, body, after_bin.empty() ? nullptr : after_bin.data(), nullptr,
+                                         after_bin.size(), cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        hytg_status st = piece == 0 ? capture_loop_body(c, algo, c->s_cap, (unsigned long long)h)
+                                    : issue_plan_tail(c, algo, 0xFFFFFFFFu, c->s_cap, c->d_loop, 2);
+        if (st == HYTG_OK && piece == 0) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            if (cudaStreamGetCaptureInfo(c->s_cap, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess || nd == 0)
+                st = fail(c, HYTG_ERR_CUDA, "device loop: no node after k_bin");
+            else
+                after_bin.assign(deps, deps + nd);
+        }
+        c->capturing = false;
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(c->s_cap, &captured);
+        if (st != HYTG_OK) { free_loop_graph(c); return st; }
+        if (e_end != cudaSuccess) {
+            free_loop_graph(c);
+            return fail(c, HYTG_ERR_CUDA, std::string("capture of the device loop: ") + cudaGetErrorString(e_end));
+        }
+    }
+    if (c->loop_fc) {
+        c->capturing = true;
+        hytg_status st = capture_loop_fc(c, algo, body, after_bin);
+        c->capturing = false;
+        if (st != HYTG_OK) { free_loop_graph(c); return st; }
     }
     cudaGraphExec_t ex = nullptr;
     const cudaError_t e_in = cudaGraphInstantiate(&ex, g, 0);
@@ -1029,9 +1280,30 @@ hytg_status ensure_loop_graph(hytg_ctx *c, int algo) {
         free_loop_graph(c);
         return fail(c, HYTG_ERR_CUDA, std::string("instantiating the device loop: ") + cudaGetErrorString(e_in));
     }
+    if (c->loop_fc && !c->loop_fh.empty())
+        CK(cudaMemcpy(c->d_loop_fh, c->loop_fh.data(), c->loop_fh.size() * 8, cudaMemcpyHostToDevice));
     c->loop_exec = ex;
     c->loop_key = key;
     return HYTG_OK;
+}
+
+// The device loop with its F and C nodes when the run allows them: first
+// with memcpy nodes for the F copies, then with a copy kernel, and if the
+// installed driver accepts neither, without F and C nodes (such iterations
+// then go to the host, as with "device_loop" 1).
+hytg_status ensure_loop_graph_fc(hytg_ctx *c, int algo) {
+    if (!loop_fc_wanted(c) || c->loop_fc_copy >= 2) {
+        c->loop_fc = false;
+        return ensure_loop_graph(c, algo);
+    }
+    for (;;) {
+        c->loop_fc = true;
+        hytg_status s = ensure_loop_graph(c, algo);
+        if (s == HYTG_OK) return s;
+        cudaGetLastError();
+        c->loop_fc = false;
+        if (++c->loop_fc_copy >= 2) return ensure_loop_graph(c, algo);
+    }
 }
 
 
@@ -1219,6 +1491,8 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             CK(cudaStreamWaitEvent(cs, c->ev_free[slot], 0));
             ScopedTime t(c, HYTG_K_COPY_F, cs);
             t.bytes = edges * ebytes;
+            t.part_first = i0;
+            t.part_last = j;
             CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, cs));
             if (n_arrays == 2)
                 CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, cs));
@@ -1240,12 +1514,16 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         {
             ScopedTime tm(c, HYTG_K_RELAX_F, fs);
             tm.edges = t.k_end - t.k_begin;
+            tm.part_first = i0;
+            tm.part_last = j;
             CK(relax_any(c, st, la, dsum, t, 8 * (int)device_sms(), fs));
         }
         if (second_pass_on(c, algo)) {
             ScopedTime tm(c, kKindSecondPass, fs);
             unsigned long long *ctr = next_sp_slot(c, &tm.sp_slot);
             tm.vertices = c->part_vb[j + 1] - c->part_vb[i0];
+            tm.part_first = i0;
+            tm.part_last = j;
             CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
                                   edges, c->part_vb[i0], c->part_vb[j + 1], e0, c->part_eb[j + 1],
                                   sp_scratch(c), ctr, c->d_err, fs));
@@ -1334,6 +1612,16 @@ hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uin
     h.max_it = (unsigned long long)c->max_iters;
     h.m = (unsigned long long)c->m;
     h.rec = c->d_loop_rec;
+    if (c->loop_fc) {
+        const PartArrays pa = part_arrays(c);
+        h.f_handles = c->d_loop_fh;
+        h.c_handle = c->loop_ch;
+        h.c_cap = c->carve.compact_edges;
+        h.route = pa.route;
+        h.part_eb = c->d_part_eb;
+        h.n_parts = (unsigned int)(c->part_vb.size() - 1);
+        h.n_arrays = c->last_run_arrays;
+    }
     iteration_mark(c);
     CK(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->s_main));
     CK(cudaGraphLaunch(c->loop_exec, c->s_main));
@@ -1351,12 +1639,16 @@ hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uin
         c->stats.route_edges[r] += h.route_edges[r];
     }
     c->stats.link_bytes[kRouteZ] += h.z_lines * (uint64_t)c->m;
+    c->stats.link_bytes[kRouteF] += h.f_bytes;
+    c->stats.link_bytes[kRouteC] += h.c_lines * (uint64_t)c->m;
+    c->stats.f_tasks += h.f_parts;
     c->stats.edges_relaxed += h.edges;
     c->stats.vertices_processed += h.vertices;
     c->stats.graph_launches += 1;
     c->stats.graph_iterations += h.iterations;
     // every body run launches the whole body; gated kernels return at once
-    c->stats.kernel_launches += (uint64_t)c->loop_kernels * ((uint64_t)(h.it - it) + 1);
+    c->stats.kernel_launches += (uint64_t)c->loop_kernels * ((uint64_t)(h.it - it) + 1) +
+                                h.f_parts * c->loop_f_kernels + h.c_iters * c->loop_c_kernels;
     it = h.it;
     bucket = h.bucket;
     status = (int)h.status;
@@ -1413,6 +1705,8 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_sp, kSpSlots * sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_link_ctr, 2 * kRoutes * sizeof(unsigned long long)));
     ck(cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
+    ck(cudaStreamCreateWithFlags(&c->s_cap2, cudaStreamNonBlocking));
+    ck(cudaMalloc(&c->d_loop_fh, 1024 * sizeof(unsigned long long)));
     ck(cudaMalloc(&c->d_loop, sizeof(LoopCtl)));
     ck(cudaMalloc(&c->d_loop_rec, (size_t)c->loop_rec_cap * sizeof(hytg_iter_record)));
     ck(cudaHostAlloc((void **)&c->h_loop, sizeof(LoopCtl), cudaHostAllocDefault));
@@ -1455,6 +1749,8 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_loop_rec);
     if (c->h_loop) cudaFreeHost(c->h_loop);
     if (c->s_cap) cudaStreamDestroy(c->s_cap);
+    if (c->s_cap2) cudaStreamDestroy(c->s_cap2);
+    dfree(c->d_loop_fh);
     delete c->pool;
     for (int i = 0; i < 2; ++i) {
         if (c->h_cstage[i]) cudaFreeHost(c->h_cstage[i]);
@@ -1493,18 +1789,11 @@ hytg_status hytg_load_csr(hytg_ctx *c, uint64_t V, uint64_t E, const uint64_t *o
         if (getenv("HYTG_INJECT_HOSTMEM_FAIL") && atoi(getenv("HYTG_INJECT_HOSTMEM_FAIL")) != 0)
             return fail(c, HYTG_ERR_HOSTMEM, "pinned allocation failure injected by HYTG_INJECT_HOSTMEM_FAIL");
         const size_t eb = std::max<uint64_t>(E, 1) * 4;
-        if (cudaHostAlloc((void **)&c->h_dst, eb, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
-            cudaGetLastError();
-            c->h_dst = nullptr;
-            return fail(c, HYTG_ERR_HOSTMEM, "cudaHostAlloc of the neighbour array failed");
-        }
-        if (weights) {
-            if (cudaHostAlloc((void **)&c->h_w, eb, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
-                cudaGetLastError();
-                c->h_w = nullptr;
-                free_graph(c);
-                return fail(c, HYTG_ERR_HOSTMEM, "cudaHostAlloc of the weight array failed");
-            }
+        if (alloc_edge_array(c, 0, &c->h_dst, eb) != HYTG_OK)
+            return fail(c, HYTG_ERR_HOSTMEM, "pinned allocation of the neighbour array failed");
+        if (weights && alloc_edge_array(c, 1, &c->h_w, eb) != HYTG_OK) {
+            free_graph(c);
+            return fail(c, HYTG_ERR_HOSTMEM, "pinned allocation of the weight array failed");
         }
         if (c->hub_frac > 0.0) {
             // hub sorting: relabel so that the hubs are internal ids [0, n_hubs)
@@ -1651,8 +1940,10 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
-    else if (k == "device_loop") { if (v != 0 && v != 1) return bad(); c->device_loop = v; }
+    else if (k == "device_loop") { if (v != 0 && v != 1 && v != 2) return bad(); c->device_loop = v; }
+    else if (k == "host_huge") { if (v != 0 && v != 1) return bad(); c->host_huge = v; }
     else if (k == "serve_frames") { if (v < 0 || v > kMaxFrames || v != std::floor(v)) return bad(); c->serve_frames_param = v; }
+    else if (k == "batch_sparse_below") { if (v < -1 || v > 65 || v != std::floor(v)) return bad(); c->batch_sparse_below = v; }
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1684,7 +1975,9 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "compact_host") *v = c->compact_host;
     else if (k == "priority") *v = c->priority;
     else if (k == "device_loop") *v = c->device_loop;
+    else if (k == "host_huge") *v = c->host_huge;
     else if (k == "serve_frames") *v = c->serve_frames_param;
+    else if (k == "batch_sparse_below") *v = c->batch_sparse_below;
     else return fail(c, HYTG_ERR_ARG, "unknown parameter " + k);
     return HYTG_OK;
 }
@@ -1742,6 +2035,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             c->batch_K = n_sources;
         }
         const int n_arrays = (algo == kSSSP) ? 2 : 1;
+        c->last_run_arrays = n_arrays;
         CK(cudaEventRecord(c->ev_run[0], c->s_main));
         hytg_status s = plan_carve(c, n_arrays);
         if (s != HYTG_OK) return s;
@@ -1769,7 +2063,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 for (uint32_t g = 0; g * kFrameSources < c->batch_K; ++g)
                     CK(launch_frame_init(c->bs, c->V, g, c->s_main));
                 CK(launch_b_init(c->bs, c->V, c->n_words_alloc, c->d_src, c->batch_K,
-                                 (float)(1.0 - c->pr_damping), st.bm_cur, c->s_main));
+                                 ppr_seed_mass(c), st.bm_cur, c->s_main));
             } else {
                 CK(launch_init(st, c->V, c->n_words_alloc, source, c->s_main));
             }
@@ -1804,7 +2098,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 // captured after iteration 0 has run, so every launcher's
                 // one-time set-up happened outside the capture; a CUDA driver that
                 // cannot build the graph leaves this context on the host loop
-                if (ensure_loop_graph(c, algo) != HYTG_OK) {
+                if (ensure_loop_graph_fc(c, algo) != HYTG_OK) {
                     c->loop_unavailable = true;
                     c->loop_error = c->err;
                     cudaGetLastError();
@@ -1938,6 +2232,8 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             r.bytes = tl.bytes;
             r.edges = tl.edges;
             r.vertices = tl.vertices;
+            r.part_first = tl.part_first;
+            r.part_last = tl.part_last;
             if (tl.sp_slot >= 0)
                 r.edges = (uint32_t)tl.sp_slot < kSpSlots - 1 && (size_t)tl.sp_slot < sp.size() ? sp[tl.sp_slot]
                                                                                             : UINT64_MAX;
@@ -2059,7 +2355,7 @@ hytg_status hytg_serve_admit(hytg_ctx *c, uint32_t slot, uint32_t source) {
         CK(launch_frame_init(c->bs, c->V, g, c->s_main));
     }
     const uint32_t src = c->permuted ? c->h_inv[source] : source;
-    CK(launch_serve_admit(c->bs, c->V, slot, src, (float)(1.0 - c->pr_damping), c->d_bm[0], c->s_main));
+    CK(launch_serve_admit(c->bs, c->V, slot, src, ppr_seed_mass(c), c->d_bm[0], c->s_main));
     c->serve_busy |= 1ull << slot;
     c->serve_admit_it[slot] = c->serve_it;
     return HYTG_OK;

@@ -1,12 +1,13 @@
 // Kernels of the device-driven iteration loop.  The host captures one
 // iteration (pre-step, counts, selection, k_loop_decide, binning, cache and
-// zero-copy relax) as the body of a CUDA-graph WHILE node; k_loop_decide
-// ends the loop when the frontier is empty, when the iteration cap is
-// reached, or when the selection (Sec. V-A) sent a partition to the F or C
-// route, whose copies the host issues (Sec. V-B task combination and
-// Sec. VI-B multi-stream scheduling stay on the host).  Iterations that use
-// only the resident cache and zero-copy routes (the long tails of tiny
-// frontiers on high-diameter graphs) then cost no host round trip.
+// zero-copy relax, and with "device_loop" 2 one IF node per partition that
+// copies it into a staging slot and relaxes it, and an IF node for the C
+// route) as the body of a CUDA-graph WHILE node; k_loop_decide ends the loop
+// when the frontier is empty, when the iteration cap is reached, or when the
+// selection (Sec. V-A) sent a partition to a route the body does not hold
+// (F or C with "device_loop" 1; a C route larger than the compaction buffer),
+// whose copies the host then issues.  Iterations run in the body cost no host
+// round trip.
 #include "common.cuh"
 #include "hytg.h"
 
@@ -20,9 +21,70 @@ __global__ void k_zero_u64(unsigned long long *p, unsigned long long n) {
         p[i] = 0ull;
 }
 
-// One thread: the host loop's decisions for the iteration just planned.
+__device__ void loop_decide_one(const Summary *sum, LoopCtl *ctl, cudaGraphConditionalHandle h);
+
+// Thread 0: the host loop's decisions for the iteration just planned; then
+// the block opens the IF nodes of the partitions routed F (each copies its
+// partition into a staging slot and relaxes it) and of the C route.
 __global__ void k_loop_decide(const Summary *sum, LoopCtl *ctl, cudaGraphConditionalHandle h) {
-    if (threadIdx.x != 0) return;
+    __shared__ unsigned long long s_parts, s_bytes;
+    if (threadIdx.x == 0) {
+        s_parts = s_bytes = 0;
+        loop_decide_one(sum, ctl, h);
+    }
+    __syncthreads();
+    // every IF condition is set on every iteration (a value set once would
+    // otherwise carry over to the next iteration of the loop), and left
+    // closed when the device does not take the iteration
+    const bool work = ctl->work != 0;
+    if (ctl->f_handles) {
+        unsigned long long np = 0, nb = 0;
+        for (unsigned int i = threadIdx.x; i < ctl->n_parts; i += blockDim.x) {
+            const bool f = work && ctl->route[i] == kRouteF;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)ctl->f_handles[i], f ? 1u : 0u);
+            if (f) {
+                ++np;
+                nb += (ctl->part_eb[i + 1] - ctl->part_eb[i]) * 4ull * ctl->n_arrays;
+            }
+        }
+        if (np) {
+            atomicAdd(&s_parts, np);
+            atomicAdd(&s_bytes, nb);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool c_on = work && sum->route_edges[kRouteC] != 0;
+        if (ctl->c_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)ctl->c_handle, c_on ? 1u : 0u);
+        if (work) {
+            hytg_iter_record *r = (hytg_iter_record *)ctl->rec + (ctl->n_rec - 1);
+            r->f_tasks = (unsigned int)s_parts;
+            r->link_bytes += s_bytes;
+            ctl->f_parts += s_parts;
+            ctl->f_bytes += s_bytes;
+            if (c_on && ctl->c_handle) {
+                ++ctl->c_iters;
+                ctl->c_lines += sum->route_lines[kRouteC];
+                r->link_bytes += sum->route_lines[kRouteC] * ctl->m;
+            }
+        }
+    }
+}
+
+// F copy inside the device loop without a memcpy node: 16-byte loads from
+// mapped host memory, coalesced, into the staging slot.
+__global__ void k_copy_words(const unsigned int *src, unsigned int *dst, unsigned long long n,
+                             const LoopCtl *loop) {
+    if (loop && !loop->work) return;
+    const unsigned long long n4 = n / 4;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    for (unsigned long long i = t0; i < n4; i += stride)
+        ((uint4 *)dst)[i] = __ldcs((const uint4 *)src + i);
+    for (unsigned long long i = n4 * 4 + t0; i < n; i += stride) dst[i] = src[i];
+}
+
+__device__ void loop_decide_one(const Summary *sum, LoopCtl *ctl, cudaGraphConditionalHandle h) {
     ctl->work = 0;
     if (sum->n_active == 0) {
         if (sum->pending == 0) {
@@ -45,7 +107,10 @@ __global__ void k_loop_decide(const Summary *sum, LoopCtl *ctl, cudaGraphConditi
         cudaGraphSetConditional(h, 0);
         return;
     }
-    if (sum->route_parts[kRouteF] != 0 || sum->route_parts[kRouteC] != 0 || ctl->n_rec >= ctl->rec_cap) {
+    const bool f_host = sum->route_parts[kRouteF] != 0 && !ctl->f_handles;
+    const bool c_host = sum->route_parts[kRouteC] != 0 &&
+                        (!ctl->c_handle || sum->route_edges[kRouteC] > ctl->c_cap);
+    if (f_host || c_host || ctl->n_rec >= ctl->rec_cap) {
         ctl->status = kLoopHost;          // the host takes this iteration from k_bin on
         cudaGraphSetConditional(h, 0);
         return;
@@ -86,7 +151,18 @@ cudaError_t launch_zero_u64(unsigned long long *p, unsigned long long n, cudaStr
 
 cudaError_t launch_loop_decide(const Summary *sum, LoopCtl *ctl, unsigned long long cond_handle,
                                cudaStream_t s) {
-    k_loop_decide<<<1, 32, 0, s>>>(sum, ctl, (cudaGraphConditionalHandle)cond_handle);
+    k_loop_decide<<<1, 256, 0, s>>>(sum, ctl, (cudaGraphConditionalHandle)cond_handle);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_words(const unsigned int *src, unsigned int *dst, unsigned long long n,
+                              const LoopCtl *loop, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (((uintptr_t)src | (uintptr_t)dst) & 15) return cudaErrorInvalidValue;
+    unsigned long long blocks = (n / 4 + 255) / 256;
+    if (blocks > 4ull * device_sms()) blocks = 4ull * device_sms();
+    if (blocks == 0) blocks = 1;
+    k_copy_words<<<(unsigned int)blocks, 256, 0, s>>>(src, dst, n, loop);
     return cudaGetLastError();
 }
 

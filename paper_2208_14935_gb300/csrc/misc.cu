@@ -21,7 +21,9 @@ __global__ void k_init(AlgoState st, unsigned long long V, unsigned long long n_
             case kSSSP: st.val[v] = (v == source) ? 0u : 0xFFFFFFFFu; break;
             case kCC: st.val[v] = (unsigned int)v; break;   // internal id, mapped at the end
             case kPR: st.rank[v] = 0.0f; st.delta[v] = base; break;
-            default: st.rank[v] = 0.0f; st.delta[v] = (v == source) ? base : 0.0f; break;
+            // PPR: the seed holds the whole initial residual of PageRank,
+            // (1 - d) V, so that eps bounds the same relative error
+            default: st.rank[v] = 0.0f; st.delta[v] = (v == source) ? base * (float)V : 0.0f; break;
         }
     }
     const bool all = (st.algo == kCC || st.algo == kPR);

@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax(AlgoState st, ListArrays 
                                                        const Summary *sum, RelaxTask t) {
     __shared__ TileSmem<false> sm;
     if (st.loop && !st.loop->work) return;
-    const unsigned long long kb = t.device_sized ? 0ull : t.k_begin;
-    const unsigned long long ke = t.device_sized ? sum->route_edges[t.route] : t.k_end;
+    unsigned long long kb, ke;
+    task_range(t, sum, kb, ke);
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
     float *hub_rep = st.hub_rep ? st.hub_rep + (size_t)(sm_id() % kHubReplicas) * st.n_hub_rep : nullptr;
@@ -131,9 +131,11 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_pair(AlgoState st, ListAr
 
 __global__ void __launch_bounds__(kRelaxBlock) k_gather(ListArrays la, const Summary *sum,
                                                         RelaxTask t, unsigned int *out_dst,
-                                                        unsigned int *out_w) {
+                                                        unsigned int *out_w, const LoopCtl *loop) {
     __shared__ TileSmem<false> sm;
-    const unsigned long long kb = t.k_begin, ke = t.k_end;
+    if (loop && !loop->work) return;
+    unsigned long long kb, ke;
+    task_range(t, sum, kb, ke);
     if (kb >= ke) return;
     const unsigned long long t_first = kb / kTile, t_last = (ke - 1) / kTile;
     for (unsigned long long tile = t_first + blockIdx.x; tile <= t_last; tile += gridDim.x) {
@@ -375,7 +377,7 @@ cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *of
 cudaError_t launch_relax(const AlgoState &st, const ListArrays &la, const Summary *sum,
                          const RelaxTask &t, int grid_cap, cudaStream_t s) {
     unsigned int grid = (unsigned int)grid_cap;
-    if (!t.device_sized) {
+    if (!t.device_sized && !t.dev_edge) {
         if (t.k_begin >= t.k_end) return cudaSuccess;
         const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
         if (tiles < grid) grid = (unsigned int)tiles;
@@ -402,11 +404,14 @@ cudaError_t launch_relax_pair(const AlgoState &st, const ListArrays &la, const S
 
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
-                          cudaStream_t s) {
-    if (t.k_begin >= t.k_end) return cudaSuccess;
-    const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
-    unsigned int grid = tiles < (unsigned long long)grid_cap ? (unsigned int)tiles : (unsigned int)grid_cap;
-    k_gather<<<grid, kRelaxBlock, 0, s>>>(la, sum, t, out_dst, out_w);
+                          cudaStream_t s, const LoopCtl *loop) {
+    unsigned int grid = (unsigned int)grid_cap;
+    if (!t.device_sized && !t.dev_edge) {
+        if (t.k_begin >= t.k_end) return cudaSuccess;
+        const unsigned long long tiles = (t.k_end - 1) / kTile - t.k_begin / kTile + 1;
+        if (tiles < grid) grid = (unsigned int)tiles;
+    }
+    k_gather<<<grid, kRelaxBlock, 0, s>>>(la, sum, t, out_dst, out_w, loop);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,24 @@ template <> struct TileSmem<true> {
     unsigned int wmax[kRelaxBlock / 32];
 };
 
+// Edge range [kb, ke) of a task in its route's edge space: the host's bounds,
+// the whole route (device_sized), or one partition's slice of the F route
+// read on the device (dev_edge; its first list entry goes to t.first_entry).
+__device__ __forceinline__ void task_range(RelaxTask &t, const Summary *sum, unsigned long long &kb,
+                                           unsigned long long &ke) {
+    if (t.dev_edge) {
+        kb = *t.dev_edge;
+        ke = kb + *t.dev_len;
+        t.first_entry = *t.dev_entry;
+    } else if (t.device_sized) {
+        kb = 0;
+        ke = sum->route_edges[t.route];
+    } else {
+        kb = t.k_begin;
+        ke = t.k_end;
+    }
+}
+
 // Set up one tile; returns the number of edges (0 if nothing to do).
 template <bool BATCH>
 __device__ __forceinline__ int tile_setup(TileSmem<BATCH> &sm, const ListArrays &la, const Summary *sum,

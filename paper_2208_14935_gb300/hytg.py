@@ -61,7 +61,7 @@ class hytg_iter_record(ctypes.Structure):
 
 class hytg_timed_launch(ctypes.Structure):
     _fields_ = [("kind", u32), ("stream", u32), ("start_ms", dbl), ("end_ms", dbl), ("bytes", u64),
-                ("edges", u64), ("vertices", u64)]
+                ("edges", u64), ("vertices", u64), ("part_first", u32), ("part_last", u32)]
 
 
 class hytg_serve_info(ctypes.Structure):
@@ -332,7 +332,7 @@ def hytg_get_timeline(ctx) -> np.ndarray:
     _check(ctx, load().hytg_get_timeline(ctx, arr, n.value, ctypes.byref(n)))
     dt = np.dtype([("kind", np.uint32), ("stream", np.uint32), ("start_ms", np.float64),
                    ("end_ms", np.float64), ("bytes", np.uint64), ("edges", np.uint64),
-                   ("vertices", np.uint64)])
+                   ("vertices", np.uint64), ("part_first", np.uint32), ("part_last", np.uint32)])
     assert dt.itemsize == ctypes.sizeof(hytg_timed_launch)
     return np.frombuffer(bytes(arr), dtype=dt, count=n.value).copy()
 

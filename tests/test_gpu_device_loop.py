@@ -106,8 +106,36 @@ def test_device_loop_reuse_and_invalidation(hy, rmat16):
 def test_device_loop_param(hy, rmat16):
     e = engine(hy, rmat16, rmat16.E)
     assert e.get_param("device_loop") == 1
+    e.set_param("device_loop", 2)
     with pytest.raises(hy.HytgError):
-        e.set_param("device_loop", 2)
+        e.set_param("device_loop", 3)
+    e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "cc", "pagerank", "ppr"])
+@pytest.mark.parametrize("force", [-1, 2, 3])
+def test_device_loop_f_and_c(hy, rmat16, rmat16_sym, algo, force):
+    """device_loop 2: iterations that send partitions to F (each copied into a
+    staging slot by its IF node, then relaxed) or C (gathered and relaxed by
+    the C node) stay in the graph; results equal the oracle and the host loop."""
+    g = rmat16_sym if algo == "cc" else rmat16
+    src = {"bfs": 0, "sssp": 0, "ppr": 5}.get(algo)
+    e = engine(hy, g, edge_bytes(g, algo) // 4, force_route=force, device_loop=2)
+    got = e.run(algo, src)
+    check(g, algo, got, 0 if src is None else src)
+    st = e.stats()
+    its = e.iterations()
+    assert sum(r["active_edges"] for r in its) == st["edges_relaxed"]
+    if force == 2:
+        # every iteration after the first (run before the graph is captured)
+        assert st["graph_iterations"] == st["iterations"] - 1 and st["f_tasks"] > 0
+        assert st["link_bytes"][2] > 0
+    elif force == -1:
+        assert st["graph_iterations"] > 0
+    e.set_param("device_loop", 0)
+    got0 = e.run(algo, src)
+    if algo in ("bfs", "sssp", "cc"):
+        assert np.array_equal(got0, got)
     e.close()
 
 
@@ -124,6 +152,9 @@ def test_device_loop_batched(hy, rmat16, algo, k, force):
     st = e.stats()
     if force == 4:
         assert st["graph_iterations"] > 0
+    if force == -1:
+        # F and C iterations stay in the graph for batched runs
+        assert st["graph_iterations"] >= st["iterations"] // 2 > 0, st
     for s, v in enumerate(src[:8] + src[-4:]):
         row = got[src.index(v)]
         if algo == "bfs":

@@ -398,3 +398,31 @@ def test_delta_first_order(hy, rmat16, algo, prio, force):
     check(rmat16, algo, e.run(algo, src), 5 if src is not None else 0)
     assert e.stats()["f_tasks"] > 0
     e.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_task_combination_matches_planner(hy, rmat16_sym, k):
+    """Alg. 1's task combination (Sec. V-B) as the engine issues it: the F
+    copies of CC's first iteration (every vertex active), read from the launch
+    timeline, are exactly the oracle planner's groups of the same routes (at
+    most k consecutive F partitions within a staging slot's capacity)."""
+    g = rmat16_sym
+    e = engine(hy, g, edge_bytes(g, "cc") // 4, k=k, device_loop=0, timing=1)
+    routes, _ = e.plan("cc", np.ones(g.V, np.uint8))
+    vb = e.partitions()
+    deg = np.diff(g.off.astype(np.int64))[e.permutation()]      # internal vertex order
+    off_int = np.concatenate([[0], np.cumsum(deg)])
+    E_part = off_int[vb[1:]] - off_int[vb[:-1]]
+    groups, _, _, _ = pl.combine_tasks([int(r) for r in routes], k=k, E_part=E_part,
+                                       cap_edges=e.info()["slot_edges"])
+    assert len(groups) > 1
+    check(g, "cc", e.run("cc"))
+    tl = e.timeline()
+    bins = np.flatnonzero(tl["kind"] == 2)
+    first = tl[bins[0]:bins[1]] if len(bins) > 1 else tl[bins[0]:]
+    copies = first[first["kind"] == 8]
+    got = [list(range(int(r["part_first"]), int(r["part_last"]) + 1)) for r in copies]
+    assert got == groups
+    relaxes = first[first["kind"] == 4]
+    assert [(int(r["part_first"]), int(r["part_last"])) for r in relaxes] == [(x[0], x[-1]) for x in groups]
+    e.close()
