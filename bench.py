@@ -183,9 +183,14 @@ def make_graphs(scale):
 def batched_vs_plain(hytg, eng, g, n_plain_sssp=16, n_plain_ppr=4):
     """Batched runs (64 BFS sources, 64 SSSP sources, 32 PPR seeds, seeded
     draws among vertices with out-edges) against the same sources run one at a
-    time, on the same engine, graph and budget.  Rate = per-source edges
-    relaxed / device time (CUDA events), i.e. the throughput a user of many
-    single-source queries gets."""
+    time, on the same engine, graph and budget.  `speedup` is the time to
+    solution per source, plain over batched (device time, CUDA events).  The
+    rate is per-source edges relaxed / device time; for BFS and SSSP the edge
+    counts are fixed by the graph, so the two ratios agree, while PPR's count
+    depends on the schedule (an iteration pushes whatever residual each seed
+    holds) and only the time ratio compares like with like.  For PPR the line
+    also gives the seed updates per second, second pass included, against the
+    frame-push probe (8 seeds per vertex and edge, with vector reductions)."""
     rng = np.random.default_rng(7)
     cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
     out = {}
@@ -193,12 +198,13 @@ def batched_vs_plain(hytg, eng, g, n_plain_sssp=16, n_plain_ppr=4):
         src = rng.choice(cand, k, replace=False).tolist()
         a = hytg.ALGOS[algo]
         hytg.hytg_run(eng.ctx, a, src)                       # warm-up
-        b_ms, b_edges = 0.0, 0
+        b_ms, b_edges, b_extra = 0.0, 0, 0
         for _ in range(2):
             hytg.hytg_run(eng.ctx, a, src)
             st = eng.stats()
             b_ms += st["device_ms"]
             b_edges += st["source_edges"]
+            b_extra += st["extra_edges"]
         p_ms, p_edges = 0.0, 0
         for v in src[:n_plain]:
             hytg.hytg_run(eng.ctx, a, [v])
@@ -207,9 +213,20 @@ def batched_vs_plain(hytg, eng, g, n_plain_sssp=16, n_plain_ppr=4):
             p_edges += st["edges_relaxed"]
         bg = b_edges / (b_ms * 1e-3) / 1e9
         pg = p_edges / (p_ms * 1e-3) / 1e9
+        per_src_b = b_ms / 2 / k
+        per_src_p = p_ms / n_plain
         out[algo] = {"sources": k, "batched_gteps": bg, "batched_ms": b_ms / 2,
-                     "plain_gteps": pg, "plain_ms_per_source": p_ms / n_plain,
-                     "plain_sources_timed": n_plain, "speedup": bg / pg if pg else None}
+                     "batched_ms_per_source": per_src_b,
+                     "plain_gteps": pg, "plain_ms_per_source": per_src_p,
+                     "plain_sources_timed": n_plain,
+                     "speedup": per_src_p / per_src_b if per_src_b else None,
+                     "gteps_ratio": bg / pg if pg else None}
+        if algo == "ppr":
+            upd = (b_edges + b_extra) / (b_ms * 1e-3) / 1e9
+            roof = {w: hytg.hytg_probe_frame_push(eng.ctx, 1 << 26, 3, w) for w in (1, 4)}
+            out[algo]["seed_updates_g_per_s"] = upd
+            out[algo]["frame_push_probe_g_per_s"] = {"scalar": roof[1], "v4": roof[4]}
+            out[algo]["frac_of_v4_probe_dense"] = upd / (8 * roof[4]) if roof[4] else None
     return out
 
 

@@ -44,7 +44,7 @@ typedef enum {
     HYTG_ERR_BUDGET = 3,    /* device budget below one staging slot plus compaction buffer */
     HYTG_ERR_HOSTMEM = 4,   /* pinned host allocation failed */
     HYTG_ERR_OVERFLOW = 5,  /* an SSSP distance reached 0xFFFFFFFE (does not fit 32 bits) */
-    HYTG_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out */
+    HYTG_ERR_TIMEOUT = 6,   /* hytg_run passed its "run_timeout_ms" deadline */
     HYTG_ERR_STATE = 7      /* call out of order (no graph loaded, no completed run) */
 } hytg_status;
 
@@ -99,8 +99,8 @@ typedef struct hytg_stats {
     uint32_t n_sources;               /* sources of the run (1 unless batched) */
     uint32_t pad_;
     uint64_t extra_edges;             /* edges relaxed by second passes over resident
-                                         partitions ("two_pass", Sec. VI-A); not in
-                                         edges_relaxed */
+                                         partitions ("two_pass", Sec. VI-A; batched PPR:
+                                         summed over seeds); not in edges_relaxed */
     double host_compact_ms;           /* host wall time spent compacting the C route on
                                          host threads ("compact_host" > 0), else 0 */
     uint64_t graph_launches;          /* launches of the device-loop graph ("device_loop") */
@@ -182,7 +182,9 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * "staging_frac", "compact_frac" (shares of the budget), "force_route"
  * (-1 cost model, 1 cache, 2 F, 3 C, 4 Z, 5 random per partition per
  * iteration), "seed" (for force_route 5), "pr_damping", "pr_eps" (FP32
- * residual threshold), "max_iters", "timing" (1: CUDA-event time per kernel
+ * residual threshold), "max_iters", "run_timeout_ms" (a deadline for each
+ * hytg_run, counted from its start; 0, the default: none; see hytg_run),
+ * "timing" (1: CUDA-event time per kernel
  * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
  * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),
  * "hub_replicas" (how many of the first hub ids get per-SM PageRank
@@ -190,7 +192,10 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * (delta-stepping bucket width for SSSP: -1 automatic, 0 off), "two_pass"
  * (after relaxing a resident F task or the cache, process once more the
  * vertices of that range that became active again, Sec. VI-A: 0 off,
- * 1 PageRank/PPR only (default), 2 every algorithm), "compact_host"
+ * 1 PageRank/PPR only (default), 2 every algorithm; batched runs and
+ * serving: PPR only), "two_pass_min_degree"
+ * (an F task's range gets its second pass only if it holds at least this
+ * many edges per vertex; default 4), "compact_host"
  * (0: the C route's active lists are gathered by a GPU kernel over mapped
  * host memory (default); n in 1..256: n host threads compact them into a
  * pinned staging chunk that one explicit copy moves to the device, the
@@ -216,13 +221,16 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * host as at 1), "serve_frames" (serving:
  * cap on the query frames hytg_serve_begin plans, 0 (default): as many as
  * the slots can use; see hytg_serve_get_info), "batch_sparse_below" (batched
- * SSSP/PPR relax: a warp whose 32 edges carry fewer active sources per edge
+ * SSSP relax: a warp whose 32 edges carry fewer active sources per edge
  * than this on average walks the sources of each lane's own edge; otherwise
  * it walks its edges with a lane per source; 0 never, 65 always; -1
- * (default): 16 for SSSP, always for PPR, the best of a sweep on R-MAT 24),
- * "host_huge" (1, default: hytg_load_csr places the edge arrays in
- * anonymous memory advised for transparent huge pages and registers it with
- * the driver, falling back to cudaHostAlloc if that fails; 0: cudaHostAlloc).
+ * (default): 16, the best of a sweep on R-MAT 24; batched PPR always keeps a
+ * lane per edge and pushes each frame of 8 seeds with two vector
+ * reductions),
+ * "host_huge" (0, default: hytg_load_csr places the edge arrays in
+ * cudaHostAlloc(Mapped|Portable) memory; 1: in anonymous memory advised for
+ * transparent huge pages, registered with the driver, falling back to
+ * cudaHostAlloc if that fails).
  * Changing "part_bytes" re-partitions the loaded graph.
  * Unknown key or value out of range: HYTG_ERR_ARG. */
 hytg_status hytg_set_param(hytg_ctx *ctx, const char *key, double value);
@@ -241,8 +249,15 @@ hytg_status hytg_get_param(hytg_ctx *ctx, const char *key, double *value);
  * with the same multiplicity (a self-loop is its own reverse); the first CC
  * run after a load checks this on the host (O(E) plus a sort of each row,
  * cached with the graph) and an asymmetric graph gives HYTG_ERR_ARG.
+ * With "run_timeout_ms" > 0 a run that has not converged by then stops at
+ * the next iteration boundary: the host checks the deadline before it issues
+ * an iteration, and inside the device loop it sets a word of mapped host
+ * memory that the loop's decision kernel reads before each iteration.  The
+ * call then waits for the work already issued (at most one more iteration),
+ * returns HYTG_ERR_TIMEOUT, and leaves the context idle and usable, with no
+ * result (hytg_fetch_result gives HYTG_ERR_STATE).
  * Errors: HYTG_ERR_ARG, HYTG_ERR_STATE (no graph or no budget),
- * HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_CUDA. */
+ * HYTG_ERR_OVERFLOW (SSSP), HYTG_ERR_TIMEOUT, HYTG_ERR_CUDA. */
 hytg_status hytg_run(hytg_ctx *ctx, hytg_algo algo, const uint32_t *sources, uint32_t n_sources);
 
 /* Copy the last run's result into caller-owned host memory `out` of
@@ -314,6 +329,16 @@ hytg_status hytg_probe_atomics(hytg_ctx *ctx, uint64_t n, uint32_t reps, double 
  * folded).  n in [1024, 2^30], n_rep <= 2^20.  Allocates device memory. */
 hytg_status hytg_probe_atomics_hub(hytg_ctx *ctx, uint64_t n, uint32_t reps, uint32_t n_rep,
                                    double *plain_gops, double *replica_gops);
+
+/* The roof of the batched PPR push: n pushes of a frame of 8 floats (one
+ * 32-byte sector) to uniform random vertices of 2^24 frames (512 MiB, more
+ * than the L2 holds, like the frames of a large batched run), each push as
+ * 8 / width reductions of `width` floats (1: red.global.add.f32; 2 or 4:
+ * the .v2 / .v4 vector forms).  Best of `reps`; *frame_gops in 1e9 frame
+ * pushes/s (seed updates/s = 8 x that).  n in [1024, 2^30].  Allocates
+ * device memory (n * 4 + 512 MiB). */
+hytg_status hytg_probe_frame_push(hytg_ctx *ctx, uint64_t n, uint32_t reps, uint32_t width,
+                                  double *frame_gops);
 
 /* Per-iteration record of the last run (up to cap records). */
 typedef struct hytg_iter_record {

@@ -29,9 +29,11 @@ __global__ void k_frame_init(BatchState b, unsigned long long V, unsigned int g)
     const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long n = V * kFrameSources;
     if (b.mode == kBatchPPR) {
+        // messages too: the vector push adds a whole frame's messages
         for (unsigned long long i = t0; i < n; i += stride) {
             b.delta[g][i] = 0.0f;
             b.rank[g][i] = 0.0f;
+            b.msg[g][i] = 0.0f;
         }
     } else {
         for (unsigned long long i = t0; i < n; i += stride) b.val[g][i] = 0xFFFFFFFFu;
@@ -244,13 +246,14 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_msbfs(BatchState b, ListA
 
 // Multi-source SSSP and batched PPR relax.  A warp loads 32 edges at once
 // (coalesced), one per lane, each with its source vertex u and the mask of
-// sources active at u.  When those masks are dense (on average 8 or more
-// sources per edge) the warp walks its edges one at a time with a lane per
-// source (SSSP: s = lane and lane + 32; PPR: s = lane), reading each
-// source's value row in one sector per frame; otherwise every lane keeps its
-// own edge and loops over the sources active at its u, so that 32 edges'
-// loads are in flight together instead of one edge's (the switch point is
-// the "batch_sparse_below" parameter).
+// sources active at u.  PPR: every lane pushes its own edge, a frame of 8
+// seeds per pair of vector reductions (ppr_push_vec).  SSSP: when the masks
+// are dense (on average "batch_sparse_below" or more sources per edge) the
+// warp walks its edges one at a time with a lane per source (s = lane and
+// lane + 32), reading each source's value row in one sector per frame;
+// otherwise every lane keeps its own edge and loops over the sources active
+// at its u, so that 32 edges' loads are in flight together instead of one
+// edge's.
 template <int MODE>
 __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, ListArrays la,
                                                               const Summary *sum, RelaxTask t,
@@ -285,6 +288,15 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                 }
             }
             if (dj == kInf) fj = 0;
+            if (MODE == kBatchPPR) {
+                // a lane per edge, a frame's 8 seeds per pair of vector reductions
+                const unsigned int m = (unsigned int)fj;
+                if (m) {
+                    atomicOr(&bm[dj >> 5], 1u << (dj & 31));
+                    ppr_push_vec(b, uj, dj, m);
+                }
+                continue;
+            }
             unsigned int pop = __popcll(fj);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
@@ -304,14 +316,6 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                         }
                     }
                     if (imp) atomicOr(&b.nxt[dj], imp);
-                } else {
-                    unsigned int m = (unsigned int)fj;
-                    if (m) atomicOr(&bm[dj >> 5], 1u << (dj & 31));
-                    while (m) {
-                        const unsigned int s = (unsigned int)(__ffs(m) - 1);
-                        m &= m - 1;
-                        atomicAdd(bdelta(b, dj, s), *bmsg(b, uj, s));
-                    }
                 }
                 continue;
             }
@@ -340,13 +344,125 @@ __global__ void __launch_bounds__(kRelaxBlock) k_relax_mswarp(BatchState b, List
                         imp |= (unsigned long long)__ballot_sync(0xffffffffu, better) << (32 * h);
                     }
                     if (lane == 0 && imp) atomicOr(&b.nxt[v], imp);
-                } else {
-                    if ((f >> lane) & 1ull) atomicAdd(bdelta(b, v, lane), *bmsg(b, u, lane));
-                    if (lane == 0 && f) atomicOr(&bm[v >> 5], 1u << (v & 31));
                 }
             }
         }
         __syncthreads();
+    }
+}
+
+// Batched PPR second pass over a resident range [vlo, vhi) whose edges sit in
+// `dst` (CSR edge shift at index 0), Sec. VI-A: the seeds whose residual at a
+// vertex of the range rose above eps during this iteration are taken again
+// and pushed along the still-resident edges.  k_bsp_take: a warp per 32
+// consecutive vertices, lanes are seeds; each vertex's taken seeds go to
+// sc.pay[v] (a 32-bit mask), the vertex's taken bit to sc.mask, and the
+// owners of the 256-edge chunks starting in its list to sc.owner.  The
+// residual is read and then subtracted with a reduction, so pushes that land
+// meanwhile (other streams' relaxes) stay for later.
+__global__ void k_bsp_take(BatchState b, const unsigned long long *off, unsigned long long vlo,
+                           unsigned long long vhi, unsigned int K, float damping, float eps,
+                           SecondPassScratch sc, unsigned long long *edges_out) {
+    if (b.loop && !b.loop->work) return;
+    const int lane = threadIdx.x & 31;
+    const bool has = lane < (int)K && b.delta[lane >> 3] != nullptr;
+    unsigned long long done = 0;
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long base = vlo + (((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5) << 5);
+         base < vhi; base += nw * 32) {
+        unsigned int bits = 0;
+        for (int q = 0; q < 32 && base + q < vhi; ++q) {
+            const unsigned long long v = base + q;
+            const unsigned long long e0 = off[v], deg = off[v + 1] - e0;
+            const float dl = has ? __ldcg(bdelta(b, v, lane)) : 0.0f;
+            const bool act = has && dl > eps;
+            if (act) {
+                atomicAdd(bdelta(b, v, lane), -dl);
+                *brank(b, v, lane) += dl;
+            }
+            const unsigned int seeds = __ballot_sync(0xffffffffu, act) & (deg ? 0xffffffffu : 0u);
+            // the vector push adds whole frames: the seeds not taken carry 0
+            // (this task's relax of v, the only reader of v's old messages,
+            // has finished on this stream)
+            if (seeds && has) *bmsg(b, v, lane) = act ? damping * dl / (float)deg : 0.0f;
+            if (lane == 0) sc.pay[v] = seeds;
+            if (seeds) {
+                bits |= 1u << q;
+                done += (unsigned long long)__popc(seeds) * deg;
+            }
+            // every chunk that starts in v's list has v as its owner, taken or
+            // not: the push starts its owner search there
+            if (deg) {
+                const unsigned long long c_beg = (e0 + kSpChunk - 1) / kSpChunk, c_end = (e0 + deg - 1) / kSpChunk + 1;
+                for (unsigned long long c = c_beg + lane; c < c_end; c += 32) sc.owner[c] = (unsigned int)v;
+            }
+        }
+        if (lane == 0) sc.mask[base >> 5] = bits;
+    }
+    if (lane == 0 && done) atomicAdd(edges_out, done);
+}
+
+// Batched PPR second-pass push: whole 256-edge chunks per warp, the owner of
+// each edge found among a window of 32 consecutive vertices; a lane keeps its
+// edge and loops over the seeds taken at the edge's source.
+__global__ void k_bsp_push(BatchState b, const unsigned long long *off, const unsigned int *dst,
+                           long long shift, unsigned long long src_len, unsigned long long vlo,
+                           unsigned long long vhi, unsigned long long E0, unsigned long long E1,
+                           SecondPassScratch sc, unsigned int *bm, unsigned int *err) {
+    if (b.loop && !b.loop->work) return;
+    if (E1 <= E0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long c_first = E0 / kSpChunk, c_last = (E1 - 1) / kSpChunk;
+    for (unsigned long long c = c_first + ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5);
+         c <= c_last; c += nwarps) {
+        const unsigned long long k0 = c * kSpChunk > E0 ? c * kSpChunk : E0;
+        const unsigned long long k1 = (c + 1) * kSpChunk < E1 ? (c + 1) * kSpChunk : E1;
+        unsigned long long u0 = c * kSpChunk >= E0 ? (unsigned long long)sc.owner[c] : vlo;
+        if (u0 < vlo || u0 >= vhi) {
+            if (lane == 0) atomicOr(err, 32u);
+            continue;
+        }
+        unsigned long long kb = k0;
+        while (kb < k1) {
+            const unsigned long long u = u0 + lane;
+            const unsigned long long su = u < vhi ? off[u] : E1;
+            const unsigned long long ue = u0 + 32 < vhi ? u0 + 32 : vhi;
+            const unsigned long long wend_all = off[ue];
+            const bool tk = u < vhi && ((sc.mask[u >> 5] >> (u & 31)) & 1u);
+            const unsigned int seeds = tk ? sc.pay[u] : 0u;
+            const unsigned int tmask = __ballot_sync(0xffffffffu, tk);
+            const unsigned long long wend = wend_all < k1 ? wend_all : k1;
+            if (tmask) {
+                for (unsigned long long r0 = kb; r0 < wend; r0 += 32) {
+                    const unsigned long long k = r0 + lane;
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const unsigned long long cand = __shfl_sync(0xffffffffu, su, own + step);
+                        if (cand <= k) own += step;
+                    }
+                    unsigned int m = __shfl_sync(0xffffffffu, seeds, own);
+                    if (k >= wend) m = 0;
+                    if (m) {
+                        const long long i = (long long)k - shift;
+                        if (i < 0 || (unsigned long long)i >= src_len) {
+                            atomicOr(err, 16u);
+                        } else {
+                            const unsigned int w = __ldg(dst + i);
+                            atomicOr(&bm[w >> 5], 1u << (w & 31));
+                            ppr_push_vec(b, u0 + own, w, m);
+                        }
+                    }
+                }
+            }
+            if (wend <= kb && ue >= vhi) {
+                if (lane == 0) atomicOr(err, 32u);
+                break;
+            }
+            if (wend > kb) kb = wend;
+            u0 += 32;
+        }
     }
 }
 
@@ -433,6 +549,27 @@ cudaError_t launch_relax_batched(const BatchState &b, const ListArrays &la, cons
     else if (b.mode == kBatchSSSP)
         k_relax_mswarp<kBatchSSSP><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
     else k_relax_mswarp<kBatchPPR><<<grid, kRelaxBlock, 0, s>>>(b, la, sum, t, bm, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_second_pass_batched(const BatchState &b, const unsigned long long *off,
+                                       const unsigned int *dst, long long shift,
+                                       unsigned long long src_len, unsigned long long vlo,
+                                       unsigned long long vhi, unsigned long long E0,
+                                       unsigned long long E1, unsigned int K, float damping, float eps,
+                                       const SecondPassScratch &sc, unsigned long long *edges_out,
+                                       unsigned int *bm, unsigned int *err, cudaStream_t s) {
+    if (vhi <= vlo) return cudaSuccess;
+    if ((vlo & 31) || b.mode != kBatchPPR) return cudaErrorInvalidValue;
+    const unsigned long long cap = 8ull * device_sms();
+    unsigned long long tb = (vhi - vlo + 255) / 256;          // 8 warps of 32 vertices per block
+    if (tb > cap) tb = cap;
+    const unsigned long long chunks = E1 > E0 ? (E1 - 1) / kSpChunk - E0 / kSpChunk + 1 : 0ull;
+    unsigned long long pb = (chunks + 7) / 8;
+    if (pb > cap) pb = cap;
+    if (pb == 0) pb = 1;
+    k_bsp_take<<<(unsigned int)tb, 256, 0, s>>>(b, off, vlo, vhi, K, damping, eps, sc, edges_out);
+    k_bsp_push<<<(unsigned int)pb, 256, 0, s>>>(b, off, dst, shift, src_len, vlo, vhi, E0, E1, sc, bm, err);
     return cudaGetLastError();
 }
 

@@ -133,7 +133,7 @@ struct GraphDev {
 // Control block of the device-driven iteration loop (a CUDA graph whose
 // WHILE node repeats plan + cache/Z relax until an iteration needs the F or C
 // route, the frontier is empty, or the iteration cap is reached).
-enum LoopStatus : unsigned int { kLoopRun = 0, kLoopDone = 1, kLoopHost = 2, kLoopMaxIt = 3 };
+enum LoopStatus : unsigned int { kLoopRun = 0, kLoopDone = 1, kLoopHost = 2, kLoopMaxIt = 3, kLoopCancel = 4 };
 struct LoopCtl {
     unsigned int status;            // LoopStatus when the loop exits
     unsigned int it;                // number of the iteration being planned
@@ -153,6 +153,9 @@ struct LoopCtl {
     const unsigned char *route;     // per-partition routes of the iteration
     const unsigned long long *part_eb;
     unsigned int n_parts, n_arrays;
+    // a word of mapped host memory that the host sets to end the loop at the
+    // next iteration boundary (a run past its deadline); nullptr: none
+    const volatile unsigned int *cancel;
     // totals over the device iterations of this launch
     unsigned long long route_parts[kRoutes], route_entries[kRoutes], route_edges[kRoutes];
     unsigned long long z_lines, vertices, edges, iterations;
@@ -218,6 +221,25 @@ __device__ __forceinline__ float *brank(const BatchState &b, unsigned long long 
 __device__ __forceinline__ float *bmsg(const BatchState &b, unsigned long long v, unsigned int s) {
     return b.msg[s >> 3] + v * kFrameSources + (s & 7);
 }
+// PPR push of u's messages along one edge u -> w for the seeds in `m` (a
+// 32-bit mask): per frame holding an active seed, the frame's 8 messages of
+// u are read as two float4 and added to w's 8 residuals with two vector
+// reductions (red.global.add.v4.f32, one L2 operation for four seeds); a
+// half with no active seed is skipped.  The other seeds of a half carry a
+// zero message (the take kernels write 0 for every seed they do not take),
+// so adding them leaves their residuals unchanged.
+__device__ __forceinline__ void ppr_push_vec(const BatchState &b, unsigned long long u, unsigned long long w,
+                                             unsigned int m) {
+    while (m) {
+        const unsigned int g = (unsigned int)(__ffs(m) - 1) >> 3;
+        const unsigned int fm = (m >> (8 * g)) & 0xFFu;
+        m &= ~(0xFFu << (8 * g));
+        const float4 *src = (const float4 *)(b.msg[g] + u * kFrameSources);
+        float4 *dst = (float4 *)(b.delta[g] + w * kFrameSources);
+        if (fm & 0x0Fu) atomicAdd(dst, __ldcg(src));
+        if (fm & 0xF0u) atomicAdd(dst + 1, __ldcg(src + 1));
+    }
+}
 constexpr unsigned int kHubReplicas = 256;
 
 cudaError_t launch_count(const GraphDev &g, const AlgoState &st, const PartArrays &pa,
@@ -269,6 +291,15 @@ cudaError_t launch_second_pass(const AlgoState &st, const unsigned long long *of
                                unsigned long long vhi, unsigned long long E0, unsigned long long E1,
                                const SecondPassScratch &sc, unsigned long long *edges_out,
                                unsigned int *err, cudaStream_t s);
+// Batched PPR: the second pass (Sec. VI-A) over a resident range, taking
+// each seed whose residual rose above eps again (K seeds).
+cudaError_t launch_second_pass_batched(const BatchState &b, const unsigned long long *off,
+                                       const unsigned int *dst, long long shift,
+                                       unsigned long long src_len, unsigned long long vlo,
+                                       unsigned long long vhi, unsigned long long E0,
+                                       unsigned long long E1, unsigned int K, float damping, float eps,
+                                       const SecondPassScratch &sc, unsigned long long *edges_out,
+                                       unsigned int *bm, unsigned int *err, cudaStream_t s);
 cudaError_t launch_gather(const ListArrays &la, const Summary *sum, const RelaxTask &t,
                           unsigned int *out_dst, unsigned int *out_w, int grid_cap,
                           cudaStream_t s, const LoopCtl *loop = nullptr);
@@ -322,6 +353,8 @@ cudaError_t launch_upload_bitmap(const unsigned char *active_dev, unsigned int *
                                  cudaStream_t s);
 cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, int skew, bool gen,
                              cudaStream_t s, float *rep = nullptr, unsigned int n_rep = 0);
+cudaError_t launch_frame_probe(const unsigned int *idx, float *d, unsigned long long n, int width,
+                               cudaStream_t s);
 cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
                             int grid, cudaStream_t s);
 

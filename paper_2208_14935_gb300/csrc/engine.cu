@@ -243,10 +243,12 @@ struct hytg_ctx {
     double hub_replicas = 4096;                          // hub ids with per-SM accumulators
     double sssp_delta = -1;                              // bucket width; -1 auto, 0 off
     double two_pass = 1;                                 // Sec. VI-A second pass: 0, 1 (PageRank), 2 (all)
+    double two_pass_min_degree = 4;                      // second pass only for ranges of at least this mean degree
+    double run_timeout_ms = 0;                           // hytg_run deadline (0: none)
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
-    double host_huge = 1;                                // edge arrays in transparent huge pages, registered
+    double host_huge = 0;                                // 1: edge arrays in transparent huge pages, registered
     double serve_frames_param = 0;                       // serving: cap on query frames (0: what the slots need)
     double batch_sparse_below = -1;                      // batched SSSP/PPR relax path switch (sources per
                                                          // edge); -1: 16 for SSSP, always for PPR
@@ -290,6 +292,9 @@ struct hytg_ctx {
     cudaGraphExec_t loop_exec = nullptr;
     std::string loop_key;                                // what the captured body depends on
     LoopCtl *d_loop = nullptr, *h_loop = nullptr;        // device control block, pinned mirror
+    unsigned int *h_cancel = nullptr, *d_cancel = nullptr;  // mapped word: end the device loop
+    bool has_deadline = false;
+    std::chrono::steady_clock::time_point run_deadline;
     hytg_iter_record *d_loop_rec = nullptr;
     uint32_t loop_rec_cap = 4096;
     uint32_t loop_kernels = 0;                           // kernels in one body iteration
@@ -335,12 +340,12 @@ void parallel_chunks(uint64_t n, const std::function<void(uint64_t, uint64_t)> &
 hytg_status alloc_edge_array_huge(hytg_ctx *c, int a, uint32_t **out, size_t bytes);
 
 // Pinned, device-mapped host memory for edge array a (0 dst, 1 weights).
-// With "host_huge" (default) an anonymous mapping advised for transparent
-// huge pages, aligned to 512 MiB (the huge-page size of a 64 KiB base-page
-// kernel; a 2 MiB one divides it) and registered with the driver, so that
-// the GPU's accesses over the link need far fewer page translations (runs
-// that alternate between contexts' arrays no longer slow down at random);
-// cudaHostAlloc if that fails or "host_huge" is 0.
+// cudaHostAlloc by default.  With "host_huge" = 1 an anonymous mapping
+// advised for transparent huge pages, aligned to 512 MiB (the huge-page size
+// of a 64 KiB base-page kernel; a 2 MiB one divides it) and registered with
+// the driver, falling back to cudaHostAlloc if that fails.  It is not the
+// default: in alternating runs it gave the slowest zero-copy and copy
+// episodes (a few runs 10-15x slower than the rest), base pages the mildest.
 hytg_status alloc_edge_array(hytg_ctx *c, int a, uint32_t **out, size_t bytes) {
     *out = nullptr;
     if (c->host_huge != 0 && alloc_edge_array_huge(c, a, out, bytes) == HYTG_OK) return HYTG_OK;
@@ -821,10 +826,37 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
 // vertices).  Results are normalised, so the scale cancels.
 float ppr_seed_mass(const hytg_ctx *c) { return (float)((1.0 - c->pr_damping) * (double)c->V); }
 
-// "two_pass": 0 off, 1 PageRank/PPR only (default), 2 every algorithm.
+// "two_pass": 0 off, 1 PageRank/PPR only (default), 2 every algorithm; in
+// batched runs (and serving) PPR only.
 bool second_pass_on(const hytg_ctx *c, int algo) {
-    if (c->batch_mode != kBatchNone || c->two_pass == 0) return false;
+    if (c->two_pass == 0) return false;
+    if (c->batch_mode != kBatchNone) return c->batch_mode == kBatchPPR;
     return c->two_pass == 2 || algo == kPR || algo == kPPR;
+}
+
+// The second pass over a resident range, single-source or batched PPR.
+cudaError_t second_pass_any(hytg_ctx *c, const AlgoState &st, const unsigned int *dst, const unsigned int *w,
+                            long long shift, unsigned long long src_len, unsigned long long vlo,
+                            unsigned long long vhi, unsigned long long E0, unsigned long long E1,
+                            unsigned long long *ctr, cudaStream_t s) {
+    if (c->batch_mode == kBatchPPR) {
+        BatchState b = c->bs;
+        b.loop = st.loop;
+        return launch_second_pass_batched(b, c->d_off, dst, shift, src_len, vlo, vhi, E0, E1, c->batch_K,
+                                          (float)c->pr_damping, (float)c->pr_eps, sp_scratch(c), ctr,
+                                          st.bm_cur, c->d_err, s);
+    }
+    return launch_second_pass(st, c->d_off, dst, w, shift, src_len, vlo, vhi, E0, E1, sp_scratch(c), ctr,
+                              c->d_err, s);
+}
+
+// An F task's range gets its second pass only if it holds at least
+// "two_pass_min_degree" edges per vertex: on ranges of low-degree vertices
+// the pass mostly scans vertices (on R-MAT 24, tasks under 2 edges per vertex
+// took 29 % of the second-pass time for 5 % of its edges), and the vertices
+// it would take stay active for the next iteration instead.
+bool range_second_pass(const hytg_ctx *c, uint64_t edges, uint64_t vertices) {
+    return (double)edges >= c->two_pass_min_degree * (double)vertices;
 }
 
 // The cache range gets its second pass only when every cached partition is
@@ -873,8 +905,7 @@ hytg_status ensure_batch(hytg_ctx *c, int mode, uint32_t out_rows) {
     }
     c->bs.mode = mode;
     c->bs.alive = c->d_alive;
-    c->bs.sparse_below = c->batch_sparse_below >= 0 ? (unsigned int)c->batch_sparse_below
-                                                    : (mode == kBatchPPR ? 65u : 16u);
+    c->bs.sparse_below = c->batch_sparse_below >= 0 ? (unsigned int)c->batch_sparse_below : 16u;
     for (auto &p : c->bs.val) p = nullptr;
     for (uint32_t g = 0; g < kMaxPprFrames; ++g) c->bs.delta[g] = c->bs.rank[g] = c->bs.msg[g] = nullptr;
     return HYTG_OK;
@@ -1002,9 +1033,8 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
         }
         if (cache_second_pass_on(c, algo)) {
             ScopedTime tm(c, kKindSecondPass, s);
-            CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
-                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], 0,
-                                  c->part_eb[c->carve.n_cached], sp_scratch(c), c->d_sp, c->d_err, s));
+            CK(second_pass_any(c, st, c->carve.cache_dst, c->carve.cache_w, 0, c->carve.cache_edges, 0,
+                               c->part_vb[c->carve.n_cached], 0, c->part_eb[c->carve.n_cached], c->d_sp, s));
             count_second_launch(c);
         }
         return HYTG_OK;
@@ -1021,9 +1051,8 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
             ScopedTime tm(c, kKindSecondPass, s);
             unsigned long long *ctr = next_sp_slot(c, &tm.sp_slot);
             tm.vertices = c->part_vb[c->carve.n_cached];
-            CK(launch_second_pass(st, c->d_off, c->carve.cache_dst, c->carve.cache_w, 0,
-                                  c->carve.cache_edges, 0, c->part_vb[c->carve.n_cached], 0,
-                                  c->part_eb[c->carve.n_cached], sp_scratch(c), ctr, c->d_err, s));
+            CK(second_pass_any(c, st, c->carve.cache_dst, c->carve.cache_w, 0, c->carve.cache_edges, 0,
+                               c->part_vb[c->carve.n_cached], 0, c->part_eb[c->carve.n_cached], ctr, s));
             count_second_launch(c);
             c->stats.second_pass_vertices += c->part_vb[c->carve.n_cached];
         }
@@ -1128,11 +1157,11 @@ hytg_status capture_loop_fc(hytg_ctx *c, int algo, cudaGraph_t cg, const std::ve
                 ScopedTime tm(c, HYTG_K_RELAX_F, c->s_cap2);
                 e = relax_any(c, st, la, sum, t, cap, c->s_cap2);
             }
-            if (e == cudaSuccess && second_pass_on(c, algo)) {
+            if (e == cudaSuccess && second_pass_on(c, algo) &&
+                range_second_pass(c, ee - eb, c->part_vb[i + 1] - c->part_vb[i])) {
                 ScopedTime tm(c, kKindSecondPass, c->s_cap2);
-                e = launch_second_pass(st, c->d_off, cv.slot_dst[L], cv.slot_w[L], (long long)e0, ee - e0,
-                                       c->part_vb[i], c->part_vb[i + 1], eb, ee, sp_scratch(c), c->d_sp,
-                                       c->d_err, c->s_cap2);
+                e = second_pass_any(c, st, cv.slot_dst[L], cv.slot_w[L], (long long)e0, ee - e0, c->part_vb[i],
+                                    c->part_vb[i + 1], eb, ee, c->d_sp, c->s_cap2);
                 count_second_launch(c);
             }
         }
@@ -1518,15 +1547,14 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             tm.part_last = j;
             CK(relax_any(c, st, la, dsum, t, 8 * (int)device_sms(), fs));
         }
-        if (second_pass_on(c, algo)) {
+        if (second_pass_on(c, algo) && range_second_pass(c, edges, c->part_vb[j + 1] - c->part_vb[i0])) {
             ScopedTime tm(c, kKindSecondPass, fs);
             unsigned long long *ctr = next_sp_slot(c, &tm.sp_slot);
             tm.vertices = c->part_vb[j + 1] - c->part_vb[i0];
             tm.part_first = i0;
             tm.part_last = j;
-            CK(launch_second_pass(st, c->d_off, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0,
-                                  edges, c->part_vb[i0], c->part_vb[j + 1], e0, c->part_eb[j + 1],
-                                  sp_scratch(c), ctr, c->d_err, fs));
+            CK(second_pass_any(c, st, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0, edges, c->part_vb[i0],
+                               c->part_vb[j + 1], e0, c->part_eb[j + 1], ctr, fs));
             count_second_launch(c);
             c->stats.second_pass_vertices += c->part_vb[j + 1] - c->part_vb[i0];
         }
@@ -1601,6 +1629,27 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
 // block, replays the graph, and folds the device iterations' records and
 // totals into the run's statistics.  On return `it` and `bucket` are those
 // of the iteration the loop stopped at and `status` says why it stopped.
+// A run past its "run_timeout_ms" deadline stops at an iteration boundary:
+// wait for everything already issued on the context's streams, so that the
+// context is idle and the next call can use it, and report the timeout.
+hytg_status run_timed_out(hytg_ctx *c, uint32_t it) {
+    cudaStream_t all[2 + kMaxStreams + kMaxSlots] = {c->s_main, c->s_c};
+    int n = 2;
+    for (int i = 0; i < kMaxStreams; ++i) all[n++] = c->s_f[i];
+    for (int i = 0; i < kMaxSlots; ++i) all[n++] = c->s_cp[i];
+    for (int i = 0; i < n; ++i)
+        if (all[i]) CK(cudaStreamSynchronize(all[i]));
+    c->have_result = false;
+    c->stats.iterations = it;
+    return fail(c, HYTG_ERR_TIMEOUT,
+                "the run passed run_timeout_ms (" + std::to_string(c->run_timeout_ms) + " ms) at iteration " +
+                    std::to_string(it) + "; its result is not available");
+}
+
+bool past_deadline(const hytg_ctx *c) {
+    return c->has_deadline && std::chrono::steady_clock::now() >= c->run_deadline;
+}
+
 hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uint64_t delta, int &status) {
     LoopCtl &h = *c->h_loop;
     std::memset(&h, 0, sizeof(LoopCtl));
@@ -1622,11 +1671,28 @@ hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uin
         h.n_parts = (unsigned int)(c->part_vb.size() - 1);
         h.n_arrays = c->last_run_arrays;
     }
+    h.cancel = c->has_deadline ? c->d_cancel : nullptr;
     iteration_mark(c);
     CK(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->s_main));
     CK(cudaGraphLaunch(c->loop_exec, c->s_main));
     CK(cudaMemcpyAsync(c->h_loop, c->d_loop, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->s_main));
-    CK(cudaStreamSynchronize(c->s_main));
+    if (c->has_deadline) {
+        // past the deadline the host sets the cancel word; k_loop_decide reads
+        // it at the next iteration boundary and ends the loop, so the launch
+        // still ends after at most one more iteration
+        for (;;) {
+            const cudaError_t q = cudaStreamQuery(c->s_main);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) CK(q);
+            if (*(volatile unsigned int *)c->h_cancel == 0u && std::chrono::steady_clock::now() >= c->run_deadline) {
+                *(volatile unsigned int *)c->h_cancel = 1u;
+                std::atomic_thread_fence(std::memory_order_seq_cst);
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+    } else {
+        CK(cudaStreamSynchronize(c->s_main));
+    }
     const uint32_t n = std::min<uint32_t>(h.n_rec, c->loop_rec_cap);
     if (n) {
         const size_t base = c->iters.size();
@@ -1710,6 +1776,11 @@ hytg_status hytg_create(hytg_ctx **out, int device) {
     ck(cudaMalloc(&c->d_loop, sizeof(LoopCtl)));
     ck(cudaMalloc(&c->d_loop_rec, (size_t)c->loop_rec_cap * sizeof(hytg_iter_record)));
     ck(cudaHostAlloc((void **)&c->h_loop, sizeof(LoopCtl), cudaHostAllocDefault));
+    ck(cudaHostAlloc((void **)&c->h_cancel, sizeof(unsigned int), cudaHostAllocMapped));
+    if (c->h_cancel) {
+        *c->h_cancel = 0u;
+        ck(cudaHostGetDevicePointer((void **)&c->d_cancel, c->h_cancel, 0));
+    }
     if (s != HYTG_OK) { hytg_destroy(c); return s; }
     *out = c;
     return HYTG_OK;
@@ -1748,6 +1819,7 @@ hytg_status hytg_destroy(hytg_ctx *c) {
     dfree(c->d_loop);
     dfree(c->d_loop_rec);
     if (c->h_loop) cudaFreeHost(c->h_loop);
+    if (c->h_cancel) cudaFreeHost(c->h_cancel);
     if (c->s_cap) cudaStreamDestroy(c->s_cap);
     if (c->s_cap2) cudaStreamDestroy(c->s_cap2);
     dfree(c->d_loop_fh);
@@ -1933,10 +2005,12 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "pr_damping") { if (v <= 0 || v >= 1) return bad(); c->pr_damping = v; }
     else if (k == "pr_eps") { if (v <= 0) return bad(); c->pr_eps = v; }
     else if (k == "max_iters") { if (v < 1) return bad(); c->max_iters = v; }
+    else if (k == "run_timeout_ms") { if (v < 0) return bad(); c->run_timeout_ms = v; }
     else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
     else if (k == "hub_frac") { if (v < 0 || v > 1) return bad(); c->hub_frac = v; }
     else if (k == "sssp_delta") { if (!(v == -1 || v >= 0) || v != std::floor(v) || v > 4e9) return bad(); c->sssp_delta = v; }
     else if (k == "two_pass") { if (v != 0 && v != 1 && v != 2) return bad(); c->two_pass = v; }
+    else if (k == "two_pass_min_degree") { if (v < 0 || v > 1e6) return bad(); c->two_pass_min_degree = v; }
     else if (k == "hub_replicas") { if (v < 0 || v > 65536 || v != std::floor(v)) return bad(); c->hub_replicas = v; }
     else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
@@ -1967,10 +2041,12 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "pr_damping") *v = c->pr_damping;
     else if (k == "pr_eps") *v = c->pr_eps;
     else if (k == "max_iters") *v = c->max_iters;
+    else if (k == "run_timeout_ms") *v = c->run_timeout_ms;
     else if (k == "timing") *v = c->timing;
     else if (k == "hub_frac") *v = c->hub_frac;
     else if (k == "sssp_delta") *v = c->sssp_delta;
     else if (k == "two_pass") *v = c->two_pass;
+    else if (k == "two_pass_min_degree") *v = c->two_pass_min_degree;
     else if (k == "hub_replicas") *v = c->hub_replicas;
     else if (k == "compact_host") *v = c->compact_host;
     else if (k == "priority") *v = c->priority;
@@ -2019,6 +2095,10 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
         }
         CK(cudaSetDevice(c->device));
         const auto t_start = std::chrono::steady_clock::now();
+        c->has_deadline = c->run_timeout_ms > 0;
+        if (c->has_deadline)
+            c->run_deadline = t_start + std::chrono::microseconds((long long)(c->run_timeout_ms * 1000.0));
+        *(volatile unsigned int *)c->h_cancel = 0u;
         c->have_result = false;
         c->stats = hytg_stats{};
         c->iters.clear();
@@ -2077,6 +2157,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             CK(cudaEventSynchronize(c->ev_sum[buf]));
             const char *hb = (const char *)c->h_sumbuf[buf];
             const Summary *hs = (const Summary *)hb;
+            if (hs->n_active != 0 && past_deadline(c)) return run_timed_out(c, it);
             if (hs->n_active == 0) {
                 if (hs->pending == 0) break;
                 // the current bucket is settled: open the next one at the
@@ -2109,6 +2190,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                 int status = 0;
                 s = run_device_loop(c, it, bucket, delta, status);
                 if (s != HYTG_OK) return s;
+                if (status == kLoopCancel) return run_timed_out(c, it);
                 if (status != kLoopHost) break;       // converged or at the cap
                 const int nb = it & 1;
                 iteration_mark(c);
@@ -2690,6 +2772,42 @@ hytg_status hytg_probe_atomics_hub(hytg_ctx *c, uint64_t n, uint32_t reps, uint3
     if (idx) cudaFree(idx);
     if (d) cudaFree(d);
     if (rp) cudaFree(rp);
+    return st;
+}
+
+hytg_status hytg_probe_frame_push(hytg_ctx *c, uint64_t n, uint32_t reps, uint32_t width, double *frame_gops) {
+    if (!c || !frame_gops || n < 1024 || n > (1ull << 30) || reps == 0 || (width != 1 && width != 2 && width != 4))
+        return HYTG_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    constexpr unsigned long long kVerts = 1ull << 24;
+    unsigned int *idx = nullptr;
+    float *d = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto run = [&]() -> hytg_status {
+        CK(cudaMalloc(&idx, n * 4));
+        CK(cudaMalloc(&d, kVerts * 8 * 4));
+        CK(cudaMemset(d, 0, kVerts * 8 * 4));
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(launch_red_probe(idx, d, n, 0, true, c->s_main));        // uniform ids in [0, 2^24)
+        float best = 1e30f;
+        for (uint32_t r = 0; r < reps + 1; ++r) {
+            CK(cudaEventRecord(a, c->s_main));
+            CK(launch_frame_probe(idx, d, n, (int)width, c->s_main));
+            CK(cudaEventRecord(b, c->s_main));
+            CK(cudaEventSynchronize(b));
+            float ms;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (r > 0) best = std::min(best, ms);
+        }
+        *frame_gops = n / (best * 1e-3) / 1e9;
+        return HYTG_OK;
+    };
+    hytg_status st = run();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (idx) cudaFree(idx);
+    if (d) cudaFree(d);
     return st;
 }
 

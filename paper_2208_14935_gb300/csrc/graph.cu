@@ -6,7 +6,8 @@
 // when the frontier is empty, when the iteration cap is reached, or when the
 // selection (Sec. V-A) sent a partition to a route the body does not hold
 // (F or C with "device_loop" 1; a C route larger than the compaction buffer),
-// whose copies the host then issues.  Iterations run in the body cost no host
+// whose copies the host then issues, or when the host has set the cancel word
+// (the run passed its deadline).  Iterations run in the body cost no host
 // round trip.
 #include "common.cuh"
 #include "hytg.h"
@@ -104,6 +105,11 @@ __device__ void loop_decide_one(const Summary *sum, LoopCtl *ctl, cudaGraphCondi
     }
     if ((unsigned long long)ctl->it >= ctl->max_it) {
         ctl->status = kLoopMaxIt;
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    if (ctl->cancel && *ctl->cancel != 0u) {
+        ctl->status = kLoopCancel;        // nothing of this iteration runs
         cudaGraphSetConditional(h, 0);
         return;
     }

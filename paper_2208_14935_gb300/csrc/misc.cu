@@ -88,9 +88,10 @@ __global__ void k_cc_jump(AlgoState st, unsigned long long n_words_alloc) {
 // CC labels (smallest internal id of each component) to the smallest
 // original id of the component, in original vertex order.
 // tmp[label] = smallest original id with that label.  Most vertices share
-// the giant component's label, so a warp whose 32 vertices all carry one
-// label reduces their ids first and issues one atomic instead of 32 to the
-// same address.
+// the giant component's label, so the lanes of a warp are grouped by label
+// (isolated vertices form groups of one), each group reduces its ids, and
+// one lane per group issues the atomic: one per distinct label instead of
+// 32 to the same address.
 __global__ void k_cc_min_orig(AlgoState st, unsigned long long V, unsigned int *tmp) {
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -100,13 +101,9 @@ __global__ void k_cc_min_orig(AlgoState st, unsigned long long V, unsigned int *
         const bool in = v < V;
         const unsigned int lab = in ? st.val[v] : 0xFFFFFFFFu;
         const unsigned int orig = in ? (st.perm ? st.perm[v] : (unsigned int)v) : 0xFFFFFFFFu;
-        const unsigned int lab0 = __shfl_sync(0xffffffffu, lab, 0);      // lane 0 is in range
-        if (__all_sync(0xffffffffu, !in || lab == lab0)) {
-            const unsigned int m = __reduce_min_sync(0xffffffffu, orig);
-            if (lane == 0) atomicMin(&tmp[lab0], m);
-        } else if (in) {
-            atomicMin(&tmp[lab], orig);
-        }
+        const unsigned int grp = __match_any_sync(0xffffffffu, lab);
+        const unsigned int m = __reduce_min_sync(grp, orig);
+        if (in && lane == __ffs(grp) - 1) atomicMin(&tmp[lab], m);
     }
 }
 __global__ void k_cc_write(AlgoState st, unsigned long long V, const unsigned int *tmp,
@@ -268,6 +265,27 @@ __global__ void k_probe_red_rep(const unsigned int *__restrict__ idx, unsigned l
     }
 }
 
+// Frame pushes, the batched PPR relax's access: each adds a frame of 8 floats
+// (32 bytes, one sector) at a vertex given by idx, as 8 / W reductions of W
+// floats each (W = 1: red.global.add.f32; 2, 4: the .v2 / .v4 forms).
+template <int W>
+__global__ void k_probe_frame(const unsigned int *__restrict__ idx, unsigned long long n, float *d) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float *p = d + (unsigned long long)__ldg(idx + i) * 8ull;
+        if (W == 4) {
+            atomicAdd((float4 *)p, make_float4(1.0f, 1.0f, 1.0f, 1.0f));
+            atomicAdd((float4 *)p + 1, make_float4(1.0f, 1.0f, 1.0f, 1.0f));
+        } else if (W == 2) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) atomicAdd((float2 *)p + j, make_float2(1.0f, 1.0f));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) atomicAdd(p + j, 1.0f);
+        }
+    }
+}
+
 inline unsigned int grid_for(unsigned long long n, unsigned int block) {
     unsigned long long g = (n + block - 1) / block;
     const unsigned long long cap = 32ull * device_sms();
@@ -356,6 +374,16 @@ cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, 
     if (gen) k_probe_idx<<<16 * device_sms(), 256, 0, s>>>(idx, n, skew);
     else if (rep && n_rep) k_probe_red_rep<<<32 * device_sms(), 256, 0, s>>>(idx, n, d, rep, n_rep);
     else k_probe_red<<<32 * device_sms(), 256, 0, s>>>(idx, n, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_probe(const unsigned int *idx, float *d, unsigned long long n, int width,
+                               cudaStream_t s) {
+    const unsigned int grid = 32 * device_sms();
+    if (width == 4) k_probe_frame<4><<<grid, 256, 0, s>>>(idx, n, d);
+    else if (width == 2) k_probe_frame<2><<<grid, 256, 0, s>>>(idx, n, d);
+    else if (width == 1) k_probe_frame<1><<<grid, 256, 0, s>>>(idx, n, d);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

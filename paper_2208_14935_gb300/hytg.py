@@ -115,6 +115,7 @@ def load(path: Optional[str] = None):
             "hytg_get_permutation": [vp, vp, u64],
             "hytg_probe_atomics": [vp, u64, u32, P(dbl), P(dbl)],
             "hytg_probe_atomics_hub": [vp, u64, u32, u32, P(dbl), P(dbl)],
+            "hytg_probe_frame_push": [vp, u64, u32, u32, P(dbl)],
             "hytg_serve_begin": [vp, i32, u32],
             "hytg_serve_admit": [vp, u32, u32],
             "hytg_serve_step": [vp, P(u64), P(u64)],
@@ -279,6 +280,14 @@ def hytg_probe_atomics_hub(ctx, n: int = 1 << 28, reps: int = 5, n_rep: int = 40
     a, b = dbl(), dbl()
     _check(ctx, load().hytg_probe_atomics_hub(ctx, int(n), reps, n_rep, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def hytg_probe_frame_push(ctx, n: int = 1 << 26, reps: int = 3, width: int = 4) -> float:
+    """1e9 pushes/s of a frame of 8 floats to random vertices, as 8 / width
+    reductions of `width` floats."""
+    a = dbl()
+    _check(ctx, load().hytg_probe_frame_push(ctx, int(n), reps, width, ctypes.byref(a)))
+    return a.value
 
 
 def hytg_serve_begin(ctx, algo: int, n_slots: int):

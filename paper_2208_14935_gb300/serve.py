@@ -234,6 +234,8 @@ def _main():
     ap.add_argument("--n", type=int, default=200, help="requests per rate")
     ap.add_argument("--rates", default="0.25,0.5,0.9", help="fractions of the saturation rate")
     ap.add_argument("--threads", action="store_true", help="one host thread per engine")
+    ap.add_argument("--both", action="store_true",
+                    help="run the rated sequence with one host thread and then with one per engine")
     ap.add_argument("--max-seconds", type=float, default=60.0,
                     help="cap on the arrival span of each rated run (fewer requests at low rates)")
     args = ap.parse_args()
@@ -265,33 +267,35 @@ def _main():
     cand = np.flatnonzero(np.diff(g.off.astype(np.int64)) > 0)
     rng = np.random.default_rng(3)
     pools = {a: rng.choice(cand, 4096, replace=True) for a in ("bfs", "sssp", "ppr")}
-    srv = Server(engines, keep_results=False, threads=args.threads)
-    # saturation: every request present at t = 0 (closed burst)
-    warm = poisson_requests(min(64, args.n), float("inf"), pools, seed=9)
-    srv.run(warm)
-    sat_reqs = poisson_requests(args.n, float("inf"), pools, seed=10)
-    sat = latency_stats(srv.run(sat_reqs))
-    mem = {}
-    for lane in srv.lanes.values():
-        hytg.hytg_serve_begin(lane.eng.ctx, hytg.ALGOS[lane.algo], lane.slots)
-        mem[lane.algo] = hytg.hytg_serve_get_info(lane.eng.ctx)
-        hytg.hytg_serve_end(lane.eng.ctx)
     out = {"metric": "served queries: p50/p99 latency and queries/s (continuous batching)",
            "graph": {"family": args.graph, "V": g.V, "E": g.E, "gen_s": round(gen_s, 1)},
            "budget_bytes": budget, "mix": "BFS:SSSP:PPR = 2:2:1", "slots": {"bfs": 64, "sssp": 64, "ppr": 32},
-           "engine_budget_bytes": {a: int(budget * shares[a] / tot) for a in shares},
-           "frames": {a: {"frames": m["frames"], "frame_bytes": m["frame_bytes"],
-                          "queries_at_once": m["frames"] * m["slots_per_frame"],
-                          "edge_budget_bytes": m["edge_budget_bytes"]} for a, m in mem.items()},
-           "host_threads": 3 if args.threads else 1,
-           "saturation": sat, "rates": {}}
-    for frac in [float(x) for x in args.rates.split(",")]:
-        rate = frac * sat["qps"]
-        n = max(8, min(args.n, int(rate * args.max_seconds)))
-        reqs = poisson_requests(n, rate, pools, seed=int(frac * 1000))
-        out["rates"][f"{frac:g}x"] = {"offered_qps": rate, **latency_stats(srv.run(reqs))}
-    out["memory_waits"] = {a: l.memory_waits for a, l in srv.lanes.items()}
-    out["max_busy"] = {a: l.max_busy for a, l in srv.lanes.items()}
+           "engine_budget_bytes": {a: int(budget * shares[a] / tot) for a in shares}, "runs": []}
+    for threads in ([False, True] if args.both else [args.threads]):
+        srv = Server(engines, keep_results=False, threads=threads)
+        # saturation: every request present at t = 0 (closed burst)
+        warm = poisson_requests(min(64, args.n), float("inf"), pools, seed=9)
+        srv.run(warm)
+        sat_reqs = poisson_requests(args.n, float("inf"), pools, seed=10)
+        sat = latency_stats(srv.run(sat_reqs))
+        if "frames" not in out:
+            mem = {}
+            for lane in srv.lanes.values():
+                hytg.hytg_serve_begin(lane.eng.ctx, hytg.ALGOS[lane.algo], lane.slots)
+                mem[lane.algo] = hytg.hytg_serve_get_info(lane.eng.ctx)
+                hytg.hytg_serve_end(lane.eng.ctx)
+            out["frames"] = {a: {"frames": m["frames"], "frame_bytes": m["frame_bytes"],
+                                 "queries_at_once": m["frames"] * m["slots_per_frame"],
+                                 "edge_budget_bytes": m["edge_budget_bytes"]} for a, m in mem.items()}
+        run = {"host_threads": 3 if threads else 1, "saturation": sat, "rates": {}}
+        for frac in [float(x) for x in args.rates.split(",")]:
+            rate = frac * sat["qps"]
+            n = max(8, min(args.n, int(rate * args.max_seconds)))
+            reqs = poisson_requests(n, rate, pools, seed=int(frac * 1000))
+            run["rates"][f"{frac:g}x"] = {"offered_qps": rate, **latency_stats(srv.run(reqs))}
+        run["memory_waits"] = {a: l.memory_waits for a, l in srv.lanes.items()}
+        run["max_busy"] = {a: l.max_busy for a, l in srv.lanes.items()}
+        out["runs"].append(run)
     print(json.dumps(out), flush=True)
     for e in engines.values():
         e.close()

@@ -70,6 +70,19 @@ def test_batched_sssp_64(hy, rmat16, force, hub):
     e.close()
 
 
+@pytest.mark.parametrize("sparse_below", [0, 65])
+def test_batched_sssp_relax_forms(hy, rmat16, sparse_below):
+    """Both forms of the batched SSSP relax (a lane per source, a lane per
+    edge looping over its sources) give every source's exact distances."""
+    g = rmat16
+    src = sources_with_out_edges(g, 40, 6)
+    e = engine(hy, g, g.E * 2, batch_sparse_below=sparse_below)
+    got = e.run("sssp", src)
+    for s, v in enumerate(src):
+        assert np.array_equal(got[s], orc.sssp(g, v)[0]), f"source {s} ({v})"
+    e.close()
+
+
 def test_batched_sssp_matches_plain_small_k(hy, rmat16):
     g = rmat16
     src = sources_with_out_edges(g, 5, 3)
@@ -80,13 +93,16 @@ def test_batched_sssp_matches_plain_small_k(hy, rmat16):
     e.close()
 
 
-@pytest.mark.parametrize("force", [-1, 4])
-def test_batched_ppr_32(hy, rmat16, force):
+@pytest.mark.parametrize("force,K", [(-1, 32), (4, 32), (2, 32), (3, 32), (2, 13), (-1, 5)])
+def test_batched_ppr(hy, rmat16, force, K):
+    """Every route (F with the batched second pass), full and partial frames
+    of 8 seeds: the vector push adds whole frames, so seeds that are not
+    taken, or do not exist, must carry zero messages."""
     g = rmat16
-    src = sources_with_out_edges(g, 32, 4)
+    src = sources_with_out_edges(g, K, 4)
     e = engine(hy, g, g.E, force_route=force)
     got = e.run("ppr", src)
-    assert got.shape == (32, g.V)
+    assert got.shape == (K, g.V)
     for s, v in enumerate(src):
         x, _, _ = orc.pagerank(g, tol=1e-13, seed=v)
         err = float(np.abs(got[s].astype(np.float64) - x).sum())

@@ -169,3 +169,31 @@ def test_device_loop_batched(hy, rmat16, algo, k, force):
     if algo != "ppr":
         assert np.array_equal(got0, got)
     e.close()
+
+
+@pytest.mark.parametrize("loop", [0, 1])
+def test_run_deadline(hy, loop):
+    """A run past "run_timeout_ms" stops at an iteration boundary with
+    HYTG_ERR_TIMEOUT (inside the device loop through the cancel word the host
+    sets, on the host loop before the next iteration), leaves no result, and
+    the same context then runs to the exact result without a deadline."""
+    g = gg.mesh(1024, 1024, shortcut_frac=0.0, wmax=1000)     # BFS: 2,047 iterations
+    e = engine(hy, g, g.E * 16, part_bytes=1 << 20, device_loop=loop)   # all cached
+    e.set_param("run_timeout_ms", 3)
+    with pytest.raises(hy.HytgError) as ex:
+        e.run("bfs", 0)
+    assert ex.value.status == hy.HYTG_ERR_TIMEOUT
+    st = e.stats()
+    assert 0 < st["iterations"] < 2047
+    with pytest.raises(hy.HytgError) as ex:
+        hy.hytg_fetch_result(e.ctx, g.V, hy.HYTG_BFS)
+    assert ex.value.status == hy.HYTG_ERR_STATE
+    e.set_param("run_timeout_ms", 0)
+    got = e.run("bfs", 0)
+    check(g, "bfs", got, 0)
+    assert e.stats()["iterations"] >= 2047
+    if loop:
+        assert e.stats()["graph_iterations"] > 0
+    e.set_param("run_timeout_ms", 60000)         # a deadline far away changes nothing
+    assert np.array_equal(e.run("bfs", 0), got)
+    e.close()

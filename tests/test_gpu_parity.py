@@ -322,6 +322,18 @@ def test_hostmem_failure_injected(hy, rmat16, monkeypatch):
     e.close()
 
 
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
+def test_host_huge_pages(hy, rmat16, algo):
+    """Edge arrays in transparent-huge-page memory registered with the driver
+    ("host_huge" = 1, off by default) give the same results on every route."""
+    e = hy.Engine(params={"part_bytes": 64 * 1024, "host_huge": 1})
+    assert e.get_param("host_huge") == 1
+    e.load(rmat16)
+    e.set_budget(edge_bytes(rmat16, algo) // 4)
+    check(rmat16, algo, e.run(algo, 0 if algo != "pagerank" else None))
+    e.close()
+
+
 def test_sssp_overflow(hy):
     g = gg.CSR(4, 3, np.array([0, 1, 2, 3, 3], np.uint64), np.array([1, 2, 3], np.uint32),
                np.array([0x7FFFFFFF, 0x7FFFFFFF, 5], np.uint32))
@@ -362,6 +374,11 @@ def test_probes(hy):
     assert mc > 1 and zc > 1
     uni, skew = e.probe_atomics(1 << 22, 2)
     assert uni > 1 and skew > 0.1
+    for width in (1, 2, 4):
+        assert hy.hytg_probe_frame_push(e.ctx, 1 << 20, 1, width) > 0.01
+    with pytest.raises(hy.HytgError) as ex:
+        hy.hytg_probe_frame_push(e.ctx, 1 << 20, 1, 3)
+    assert ex.value.status == hy.HYTG_ERR_ARG
     e.close()
 
 
@@ -370,11 +387,17 @@ def test_probes(hy):
 def test_two_pass(hy, rmat16, rmat16_sym, algo, force):
     """Second pass over resident partitions (Sec. VI-A) leaves results unchanged."""
     g = rmat16_sym if algo == "cc" else rmat16
-    e = engine(hy, g, edge_bytes(g, algo) // 4, two_pass=2, force_route=force, seed=3)
+    e = engine(hy, g, edge_bytes(g, algo) // 4, two_pass=2, force_route=force, seed=3,
+               two_pass_min_degree=0)
     src = {"bfs": 0, "sssp": 0, "ppr": 5}.get(algo)
     check(g, algo, e.run(algo, src), 0 if src is None else src)
     if force == 2 and algo != "ppr":
         assert e.stats()["extra_edges"] > 0
+    # ranges below the minimum mean degree get no second pass; results stay
+    e.set_param("two_pass_min_degree", 1e6)
+    check(g, algo, e.run(algo, src), 0 if src is None else src)
+    if force == 2:
+        assert e.stats()["extra_edges"] == 0
     e.close()
 
 
