@@ -2381,10 +2381,14 @@ hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
     const uint64_t pool_bytes = c->budget + kPoolSlack;
     uint32_t nf = (n_slots + kFrameSources - 1) / kFrameSources;
     if (c->serve_frames_param > 0) nf = std::min<uint32_t>(nf, (uint32_t)c->serve_frames_param);
+    std::string why = "the budget is smaller than one frame";
     for (; nf >= 1; --nf) {
         if ((uint64_t)nf * fb + kPoolSlack >= c->budget) continue;
         const uint64_t eb = c->budget - (uint64_t)nf * fb - kPoolSlack;
-        if (plan_carve(c, n_arrays, eb) != HYTG_OK) continue;
+        if (plan_carve(c, n_arrays, eb) != HYTG_OK) {
+            why = c->err;
+            continue;
+        }
         const uint64_t base = (c->carve.end + 255) & ~uint64_t(255);
         if (base + (uint64_t)nf * fb > pool_bytes) continue;
         c->serve_frame_base = (char *)c->d_pool + base;
@@ -2395,7 +2399,8 @@ hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
         c->batch_mode = kBatchNone;
         c->carve = Carve();
         return fail(c, HYTG_ERR_BUDGET, "the device budget holds no query frame (" + std::to_string(fb) +
-                                            " B for 8 queries) beside the smallest edge-side carve");
+                                            " B for 8 queries) beside the smallest edge-side carve; with one "
+                                            "frame: " + why);
     }
     c->serve_frames = nf;
     c->serve_frame_bytes = fb;
