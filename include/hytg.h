@@ -123,6 +123,10 @@ typedef struct hytg_stats {
                                          (and C with "compact_host"): the bytes copied;
                                          cache 0.  Index: hytg_route */
     uint64_t link_line_bytes[5];      /* the same count at 128-byte lines, times 128 */
+    uint64_t f_reused_tasks;          /* F tasks run from a staging slot that still held
+                                         their partitions ("slot_reuse"): no copy */
+    uint64_t f_reused_bytes;          /* the bytes those tasks did not copy (not in
+                                         link_bytes) */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -184,6 +188,9 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * iteration), "seed" (for force_route 5), "pr_damping", "pr_eps" (FP32
  * residual threshold), "max_iters", "run_timeout_ms" (a deadline for each
  * hytg_run, counted from its start; 0, the default: none; see hytg_run),
+ * "slot_reuse" (1: an F task whose partitions a staging slot still holds
+ * from an earlier iteration or run runs from it without a copy, counted in
+ * f_reused_tasks / f_reused_bytes; 0, the default: every F task is copied),
  * "timing" (1: CUDA-event time per kernel
  * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
  * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),

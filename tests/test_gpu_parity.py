@@ -334,6 +334,34 @@ def test_host_huge_pages(hy, rmat16, algo):
     e.close()
 
 
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
+def test_staging_slot_reuse(hy, rmat16, algo):
+    """F tasks that a staging slot still holds run without a copy; results
+    are unchanged, and for BFS/SSSP (whose F sets per iteration do not
+    depend on the order of the tasks) copied plus reused bytes equal the
+    bytes copied with reuse off.  BFS/SSSP run on a mesh, whose frontier
+    band stays in the same few partitions for many iterations."""
+    if algo == "pagerank":
+        g, pb = rmat16, 64 * 1024
+    else:
+        g, pb = gg.mesh(256, 128, shortcut_frac=0.0, wmax=1000), 16384
+    runs = {}
+    for reuse in (0, 1):
+        e = engine(hy, g, edge_bytes(g, algo) // 4, part_bytes=pb, force_route=2, slot_reuse=reuse)
+        assert e.get_param("slot_reuse") == reuse
+        src = None if algo == "pagerank" else 0
+        for _ in range(2):                     # the second run can reuse the first's slots
+            check(g, algo, e.run(algo, src))
+        runs[reuse] = e.stats()
+        e.close()
+    off, on = runs[0], runs[1]
+    assert off["f_reused_tasks"] == 0 and off["f_reused_bytes"] == 0
+    assert on["f_reused_tasks"] > 0
+    if algo != "pagerank":
+        assert on["link_bytes"][2] + on["f_reused_bytes"] == off["link_bytes"][2]
+        assert on["f_tasks"] == off["f_tasks"]
+
+
 def test_sssp_overflow(hy):
     g = gg.CSR(4, 3, np.array([0, 1, 2, 3, 3], np.uint64), np.array([1, 2, 3], np.uint32),
                np.array([0x7FFFFFFF, 0x7FFFFFFF, 5], np.uint32))
