@@ -127,6 +127,10 @@ typedef struct hytg_stats {
                                          their partitions ("slot_reuse"): no copy */
     uint64_t f_reused_bytes;          /* the bytes those tasks did not copy (not in
                                          link_bytes) */
+    uint64_t f_ahead_tasks;           /* F tasks copied ahead at the end of an iteration for
+                                         the next one ("f_ahead"); their bytes are in
+                                         link_bytes whether or not the next iteration used them */
+    uint64_t f_ahead_hits;            /* tasks that ran from such a copy instead of copying */
 } hytg_stats;
 
 /* kernel kinds indexing kernel_ms / kernel_count */
@@ -191,6 +195,14 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * "slot_reuse" (1: an F task whose partitions a staging slot still holds
  * from an earlier iteration or run runs from it without a copy, counted in
  * f_reused_tasks / f_reused_bytes; 0, the default: every F task is copied),
+ * "f_ahead" (n in 1..15 and below the number of staging slots: at the end
+ * of each host-issued iteration of a single-source run, copy that
+ * iteration's first n F tasks into the least
+ * recently used staging slots, as a guess at the next iteration's first
+ * tasks, while the link would otherwise idle through the iteration's last
+ * relaxes and the next planning; a next-iteration task found among them runs
+ * from its slot, in its place in the order; counted in f_ahead_tasks /
+ * f_ahead_hits; when on, "slot_reuse" is not applied; 0: off),
  * "timing" (1: CUDA-event time per kernel
  * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
  * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),

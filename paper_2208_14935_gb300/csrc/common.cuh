@@ -355,6 +355,8 @@ cudaError_t launch_red_probe(unsigned int *idx, float *d, unsigned long long n, 
                              cudaStream_t s, float *rep = nullptr, unsigned int n_rep = 0);
 cudaError_t launch_frame_probe(const unsigned int *idx, float *d, unsigned long long n, int width,
                                cudaStream_t s);
+cudaError_t launch_stage_copy(const unsigned int *src, unsigned int *dst, unsigned long long n,
+                              unsigned int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
                             int grid, cudaStream_t s);
 

@@ -246,6 +246,8 @@ struct hytg_ctx {
     double two_pass_min_degree = 4;                      // second pass only for ranges of at least this mean degree
     double run_timeout_ms = 0;                           // hytg_run deadline (0: none)
     double slot_reuse = 0;                               // 1: run F tasks from slots that still hold them
+    double f_ahead = 0;                                  // F tasks copied ahead for the next iteration
+    double f_copy = 0;                                   // F copies: 0 copy engine, n: copy kernel, n blocks/SM
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
@@ -268,6 +270,14 @@ struct hytg_ctx {
     // what each staging slot holds for "slot_reuse": partitions [i0, j] with
     // n_arrays arrays (n_arrays 0: nothing known)
     struct SlotHeld { uint32_t i0 = 0, j = 0; int n_arrays = 0; } slot_held[kMaxSlots];
+    // copies ahead ("f_ahead"): the slots that the end of one iteration filled
+    // with partitions [i0, j] for the next host-issued iteration (work_seq ==
+    // ahead_seq), and the position of the slot ring, which then continues
+    // across iterations so that copies ahead take the least recently used slots
+    struct AheadCopy { uint32_t slot, i0, j; int n_arrays; };
+    std::vector<AheadCopy> ahead;
+    uint64_t work_seq = 0, ahead_seq = 0;
+    uint32_t ring_pos = 0;
     std::vector<std::pair<size_t, cudaEvent_t>> iter_ev; // (iteration index, start mark), timing on
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
@@ -844,6 +854,37 @@ AlgoState algo_state(hytg_ctx *c, int algo, unsigned int bucket_limit = 0xFFFFFF
 // 1 - d at the seed alone, eps = 1e-9 left an L1 error near 0.1 on 2^24
 // vertices).  Results are normalised, so the scale cancels.
 float ppr_seed_mass(const hytg_ctx *c) { return (float)((1.0 - c->pr_damping) * (double)c->V); }
+
+// Copies ahead apply to single-source runs whose F iterations the host
+// issues (batched runs and serving keep their F iterations in the graph or
+// interleave queries, so a guess from the previous iteration does not hold).
+bool ahead_on(const hytg_ctx *c) {
+    return c->f_ahead > 0 && c->batch_mode == kBatchNone && !c->serving;
+}
+
+// Drop the copies ahead of the last iteration; the main stream (and so all
+// later work of the run) waits for those still in flight, since the next
+// user of their slots may be a graph node or a run with another carve.
+cudaError_t ahead_join(hytg_ctx *c) {
+    for (const hytg_ctx::AheadCopy &a : c->ahead) {
+        cudaError_t e = cudaStreamWaitEvent(c->s_main, c->ev_copied[a.slot], 0);
+        if (e != cudaSuccess) return e;
+    }
+    c->ahead.clear();
+    return cudaSuccess;
+}
+
+// At the start of a run or a serving session: copies ahead left by a run
+// that ended early (an error) finish before the slots can be carved again.
+cudaError_t ahead_drop(hytg_ctx *c) {
+    for (const hytg_ctx::AheadCopy &a : c->ahead) {
+        cudaError_t e = cudaStreamSynchronize(c->s_cp[a.slot]);
+        if (e != cudaSuccess) return e;
+    }
+    c->ahead.clear();
+    c->ring_pos = 0;
+    return cudaSuccess;
+}
 
 // "two_pass": 0 off, 1 PageRank/PPR only (default), 2 every algorithm; in
 // batched runs (and serving) PPR only.
@@ -1534,7 +1575,30 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     hit.assign(tasks.size(), -1);
     order.clear();
     uint32_t reserved = 0;                    // bit s: slot s serves a task of this iteration from memory
-    if (c->slot_reuse != 0) {
+    // Copies ahead ("f_ahead" > 0; single-source runs on the host loop): the
+    // end of the previous iteration copied its first tasks into slots, as a
+    // guess at this iteration's first tasks, while the link would otherwise
+    // idle through that iteration's last relaxes and this iteration's
+    // planning.  A task found among them runs from its slot and keeps its
+    // place in the order; until it is issued, copied tasks skip its slot.
+    const bool ahead = ahead_on(c);
+    uint32_t pending = 0;                     // bit s: slot s holds a copy ahead for a task not issued yet
+    uint32_t missed = 0;                      // bit s: slot s holds a copy ahead that no task uses
+    for (const hytg_ctx::AheadCopy &a : c->ahead) {
+        bool used = false;
+        if (ahead && c->ahead_seq == c->work_seq)
+            for (size_t k = 0; k < tasks.size() && !used; ++k)
+                if (hit[k] < 0 && a.n_arrays == n_arrays && tasks[k].i == a.i0 && tasks[k].j == a.j) {
+                    hit[k] = (int)a.slot;
+                    pending |= 1u << a.slot;
+                    used = true;
+                }
+        if (!used) missed |= 1u << a.slot;
+    }
+    c->ahead.clear();
+    if (ahead) {
+        for (size_t k = 0; k < tasks.size(); ++k) order.push_back((uint32_t)k);
+    } else if (c->slot_reuse != 0) {
         for (size_t k = 0; k < tasks.size(); ++k)
             for (uint32_t s = 0; s < cv.n_slots; ++s) {
                 const hytg_ctx::SlotHeld &h = c->slot_held[s];
@@ -1546,8 +1610,9 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
                 }
             }
     }
-    for (size_t k = 0; k < tasks.size(); ++k)
-        if (hit[k] < 0) order.push_back((uint32_t)k);
+    if (!ahead)
+        for (size_t k = 0; k < tasks.size(); ++k)
+            if (hit[k] < 0) order.push_back((uint32_t)k);
     // Tasks take the F compute streams in turn, and copied tasks take all the
     // slots in turn, reused ones included: those tasks were issued first, so
     // the copy into such a slot waits only for that task's relax, and the
@@ -1556,7 +1621,32 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     // a later task runs while earlier tasks' relaxes and second passes still
     // hold their slots.
     const uint32_t n_fs = std::max<uint32_t>(1, std::min<uint32_t>(cv.n_slots, (uint32_t)c->streams));
-    uint32_t rr = 0;
+    uint32_t rr = ahead ? c->ring_pos : 0;
+    // An F copy by the copy engine moves the task's edges exactly; the copy
+    // kernel ("f_copy" > 0) starts at the 16-byte boundary at or below the
+    // first edge, so the slot then holds up to 3 words before it (when it has
+    // room for them).  base_of gives the first edge a slot holds for a task.
+    auto by_kernel = [&](uint64_t e0, uint64_t edges) {
+        return c->f_copy > 0 && edges + (e0 & 3) <= cv.slot_edges;
+    };
+    auto base_of = [&](uint64_t e0, uint64_t edges) -> uint64_t {
+        return by_kernel(e0, edges) ? (e0 & ~uint64_t(3)) : e0;
+    };
+    auto copy_task = [&](uint32_t slot, uint64_t e0, uint64_t edges, cudaStream_t cs) -> cudaError_t {
+        cudaError_t e;
+        if (by_kernel(e0, edges)) {
+            const uint64_t ea = e0 & ~uint64_t(3);
+            e = launch_stage_copy(c->m_dst + ea, cv.slot_dst[slot], e0 + edges - ea, (unsigned)c->f_copy, cs);
+            if (e == cudaSuccess && n_arrays == 2)
+                e = launch_stage_copy(c->m_w + ea, cv.slot_w[slot], e0 + edges - ea, (unsigned)c->f_copy, cs);
+            c->stats.kernel_launches += n_arrays;
+        } else {
+            e = cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess && n_arrays == 2)
+                e = cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, cs);
+        }
+        return e;
+    };
     for (uint32_t k : order) {
         const FTask &ft = tasks[k];
         const uint32_t i0 = ft.i, j = ft.j;
@@ -1565,8 +1655,11 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         uint32_t slot;
         if (reuse) {
             slot = (uint32_t)hit[k];
+            pending &= ~(1u << slot);
         } else {
-            slot = rr++ % cv.n_slots;
+            // at most f_ahead < n_slots slots are pending, so this ends
+            do slot = rr++ % cv.n_slots;
+            while ((pending >> slot) & 1u);
         }
         const uint32_t fi = n_tasks % n_fs;
         cudaStream_t fs = c->s_f[fi], cs = c->s_cp[slot];
@@ -1578,15 +1671,16 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             CK(cudaStreamWaitEvent(cs, c->ev_free[slot], 0));
             {
                 ScopedTime t(c, HYTG_K_COPY_F, cs);
-                t.bytes = edges * ebytes;
+                t.bytes = (e0 + edges - base_of(e0, edges)) * ebytes;
                 t.part_first = i0;
                 t.part_last = j;
-                CK(cudaMemcpyAsync(cv.slot_dst[slot], c->h_dst + e0, edges * 4, cudaMemcpyHostToDevice, cs));
-                if (n_arrays == 2)
-                    CK(cudaMemcpyAsync(cv.slot_w[slot], c->h_w + e0, edges * 4, cudaMemcpyHostToDevice, cs));
+                CK(copy_task(slot, e0, edges, cs));
             }
             CK(cudaEventRecord(c->ev_copied[slot], cs));
             c->slot_held[slot] = {i0, j, n_arrays};
+        } else if (ahead) {
+            // copied ahead: its bytes were counted when the copy was issued
+            c->stats.f_ahead_hits += 1;
         } else {
             // the slot's last copy finished before the previous iteration
             // ended (its relax waited for it, and the main stream for that)
@@ -1597,15 +1691,17 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             f_streams_used.push_back((int)fi);
             CK(cudaStreamWaitEvent(fs, c->ev_bin, 0));
         }
-        if (!reuse) CK(cudaStreamWaitEvent(fs, c->ev_copied[slot], 0));
+        // a copy ahead may still be in flight; a reused slot's copy is not
+        if (!reuse || ahead) CK(cudaStreamWaitEvent(fs, c->ev_copied[slot], 0));
+        const uint64_t ea = base_of(e0, edges);
         RelaxTask t{};
         t.route = kRouteF; t.mode = kModeDevice; t.dst = cv.slot_dst[slot]; t.w = cv.slot_w[slot];
-        t.shift = (long long)e0;
+        t.shift = (long long)ea;
         t.k_begin = p_redge[i0];
         t.k_end = p_redge[j] + p_edges[j];
         t.first_entry = p_rentry[i0];
         t.device_sized = false;
-        t.src_len = edges;
+        t.src_len = e0 + edges - ea;
         {
             ScopedTime tm(c, HYTG_K_RELAX_F, fs);
             tm.edges = t.k_end - t.k_begin;
@@ -1619,13 +1715,13 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             tm.vertices = c->part_vb[j + 1] - c->part_vb[i0];
             tm.part_first = i0;
             tm.part_last = j;
-            CK(second_pass_any(c, st, cv.slot_dst[slot], cv.slot_w[slot], (long long)e0, edges, c->part_vb[i0],
-                               c->part_vb[j + 1], e0, c->part_eb[j + 1], ctr, fs));
+            CK(second_pass_any(c, st, cv.slot_dst[slot], cv.slot_w[slot], (long long)ea, e0 + edges - ea,
+                               c->part_vb[i0], c->part_vb[j + 1], e0, c->part_eb[j + 1], ctr, fs));
             count_second_launch(c);
             c->stats.second_pass_vertices += c->part_vb[j + 1] - c->part_vb[i0];
         }
         CK(cudaEventRecord(c->ev_free[slot], fs));
-        if (!reuse) f_bytes += edges * ebytes;
+        if (!reuse) f_bytes += (e0 + edges - ea) * ebytes;
         ++n_tasks;
     }
     // --- C: gather active lists into the compaction buffer, relax, in chunks
@@ -1662,6 +1758,40 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
         CK(cudaEventRecord(c->ev_f[sl], c->s_f[sl]));
         CK(cudaStreamWaitEvent(c->s_main, c->ev_f[sl], 0));
     }
+    // a copy ahead that no task used is still joined, so that the run's end
+    // (and its device time) covers every copy it issued
+    for (uint32_t sl = 0; sl < (uint32_t)kMaxSlots; ++sl)
+        if ((missed >> sl) & 1u) CK(cudaStreamWaitEvent(c->s_main, c->ev_copied[sl], 0));
+    // --- copies ahead for the next iteration: this iteration's first tasks,
+    // into the least recently used slots of the ring; each waits only for
+    // its slot's last relax, and the main stream does not wait for them
+    if (ahead && !tasks.empty()) {
+        const uint32_t n_ahead = std::min<uint32_t>({(uint32_t)c->f_ahead, cv.n_slots - 1, (uint32_t)order.size()});
+        for (uint32_t q = 0; q < n_ahead; ++q) {
+            const FTask &ft = tasks[order[q]];
+            const uint32_t slot = rr++ % cv.n_slots;
+            const uint64_t e0 = c->part_eb[ft.i];
+            cudaStream_t cs = c->s_cp[slot];
+            c->slot_held[slot] = hytg_ctx::SlotHeld();
+            CK(cudaStreamWaitEvent(cs, c->ev_free[slot], 0));
+            const uint64_t words = e0 + ft.edges - base_of(e0, ft.edges);
+            {
+                ScopedTime t(c, HYTG_K_COPY_F, cs);
+                t.bytes = words * ebytes;
+                t.part_first = ft.i;
+                t.part_last = ft.j;
+                CK(copy_task(slot, e0, ft.edges, cs));
+            }
+            CK(cudaEventRecord(c->ev_copied[slot], cs));
+            c->slot_held[slot] = {ft.i, ft.j, n_arrays};
+            c->ahead.push_back({slot, ft.i, ft.j, n_arrays});
+            c->stats.f_ahead_tasks += 1;
+            f_bytes += words * ebytes;
+        }
+        c->ahead_seq = c->work_seq + 1;
+    }
+    if (ahead) c->ring_pos = rr % std::max<uint32_t>(1, cv.n_slots);
+    ++c->work_seq;
     // --- statistics of this iteration
     uint64_t act_edges = 0;
     for (int r = 0; r < kRoutes; ++r) {
@@ -1705,6 +1835,7 @@ hytg_status run_timed_out(hytg_ctx *c, uint32_t it) {
     for (int i = 0; i < kMaxSlots; ++i) all[n++] = c->s_cp[i];
     for (int i = 0; i < n; ++i)
         if (all[i]) CK(cudaStreamSynchronize(all[i]));
+    c->ahead.clear();
     c->have_result = false;
     c->stats.iterations = it;
     return fail(c, HYTG_ERR_TIMEOUT,
@@ -1738,7 +1869,12 @@ hytg_status run_device_loop(hytg_ctx *c, uint32_t &it, unsigned int &bucket, uin
         h.n_arrays = c->last_run_arrays;
     }
     h.cancel = c->has_deadline ? c->d_cancel : nullptr;
-    if (c->loop_fc) slots_forget(c);      // the graph's F nodes copy into the slots
+    if (c->loop_fc) {
+        // the graph's F nodes copy into the slots: copies ahead end first
+        // (the graph is launched on the main stream) and are dropped
+        CK(ahead_join(c));
+        slots_forget(c);
+    }
     iteration_mark(c);
     CK(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->s_main));
     CK(cudaGraphLaunch(c->loop_exec, c->s_main));
@@ -2074,6 +2210,8 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "max_iters") { if (v < 1) return bad(); c->max_iters = v; }
     else if (k == "run_timeout_ms") { if (v < 0) return bad(); c->run_timeout_ms = v; }
     else if (k == "slot_reuse") { if (v != 0 && v != 1) return bad(); c->slot_reuse = v; if (v == 0) slots_forget(c); }
+    else if (k == "f_ahead") { if (v < 0 || v > kMaxSlots - 1 || v != std::floor(v)) return bad(); c->f_ahead = v; }
+    else if (k == "f_copy") { if (v < 0 || v > 32 || v != std::floor(v)) return bad(); c->f_copy = v; slots_forget(c); }
     else if (k == "timing") { c->timing = v != 0 ? 1 : 0; }
     else if (k == "hub_frac") { if (v < 0 || v > 1) return bad(); c->hub_frac = v; }
     else if (k == "sssp_delta") { if (!(v == -1 || v >= 0) || v != std::floor(v) || v > 4e9) return bad(); c->sssp_delta = v; }
@@ -2111,6 +2249,8 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "max_iters") *v = c->max_iters;
     else if (k == "run_timeout_ms") *v = c->run_timeout_ms;
     else if (k == "slot_reuse") *v = c->slot_reuse;
+    else if (k == "f_ahead") *v = c->f_ahead;
+    else if (k == "f_copy") *v = c->f_copy;
     else if (k == "timing") *v = c->timing;
     else if (k == "hub_frac") *v = c->hub_frac;
     else if (k == "sssp_delta") *v = c->sssp_delta;
@@ -2163,6 +2303,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                             "multiplicity); symmetrise the graph first");
         }
         CK(cudaSetDevice(c->device));
+        CK(ahead_drop(c));
         const auto t_start = std::chrono::steady_clock::now();
         c->has_deadline = c->run_timeout_ms > 0;
         if (c->has_deadline)
@@ -2275,6 +2416,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             if (s != HYTG_OK) return s;
         }
         c->stats.iterations = it;
+        CK(ahead_join(c));
         // finalisation
         {
             AlgoState st = algo_state(c, algo);
@@ -2431,6 +2573,7 @@ hytg_status hytg_serve_begin(hytg_ctx *c, hytg_algo algo_in, uint32_t n_slots) {
     if (!c->d_pool) return fail(c, HYTG_ERR_STATE, "no device budget set");
     if (algo == kSSSP && !c->weighted) return fail(c, HYTG_ERR_ARG, "SSSP needs edge weights");
     CK(cudaSetDevice(c->device));
+    CK(ahead_drop(c));
     const int mode = algo == kBFS ? kBatchBFS : algo == kSSSP ? kBatchSSSP : kBatchPPR;
     hytg_status s = ensure_batch(c, mode, 1);
     if (s != HYTG_OK) return s;

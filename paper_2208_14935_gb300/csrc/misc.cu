@@ -203,6 +203,29 @@ __global__ void k_zc_probe(const uint4 *src, unsigned long long n16, unsigned lo
     if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);
 }
 
+// F-route copy by the SMs ("f_copy" > 0), in place of the copy engine: the
+// words [0, n) of mapped host memory into a staging slot, both 16-byte
+// aligned, with 16-byte loads, four in flight per thread; the last n % 4
+// words one at a time.
+__global__ void __launch_bounds__(256) k_stage_copy(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                                    unsigned long long n) {
+    const unsigned long long n4 = n / 4;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long i = t0;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        const uint4 a = __ldg(src + i), b = __ldg(src + i + stride);
+        const uint4 c = __ldg(src + i + 2 * stride), d = __ldg(src + i + 3 * stride);
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n4; i += stride) dst[i] = __ldg(src + i);
+    if (t0 < n - n4 * 4)
+        ((unsigned int *)dst)[n4 * 4 + t0] = __ldg((const unsigned int *)src + n4 * 4 + t0);
+}
+
 // L2 reduction probe: indices into a 2^24-float array, uniform or with the
 // R-MAT in-degree skew (each of 24 bits set with probability 0.24), then
 // n fire-and-forget float additions.
@@ -390,6 +413,18 @@ cudaError_t launch_frame_probe(const unsigned int *idx, float *d, unsigned long 
 cudaError_t launch_zc_probe(const uint4 *src, unsigned long long n16, unsigned long long *sink,
                             int grid, cudaStream_t s) {
     k_zc_probe<<<grid, 256, 0, s>>>(src, n16, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_copy(const unsigned int *src, unsigned int *dst, unsigned long long n,
+                              unsigned int blocks_per_sm, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15) || blocks_per_sm == 0) return cudaErrorInvalidValue;
+    unsigned long long blocks = (n / 4 + 255) / 256;
+    const unsigned long long cap = (unsigned long long)blocks_per_sm * device_sms();
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    k_stage_copy<<<(unsigned int)blocks, 256, 0, s>>>((const uint4 *)src, (uint4 *)dst, n);
     return cudaGetLastError();
 }
 

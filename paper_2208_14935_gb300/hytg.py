@@ -44,7 +44,8 @@ class hytg_stats(ctypes.Structure):
                 ("second_pass_ms", dbl), ("second_pass_count", u64), ("second_pass_vertices", u64),
                 ("route_busy_ms", dbl * 5), ("kernel_busy_ms", dbl * 13),
                 ("link_sector_bytes", u64 * 5), ("link_line_bytes", u64 * 5),
-                ("f_reused_tasks", u64), ("f_reused_bytes", u64)]
+                ("f_reused_tasks", u64), ("f_reused_bytes", u64),
+                ("f_ahead_tasks", u64), ("f_ahead_hits", u64)]
 
 
 class hytg_info(ctypes.Structure):

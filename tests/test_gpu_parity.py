@@ -362,6 +362,74 @@ def test_staging_slot_reuse(hy, rmat16, algo):
         assert on["f_tasks"] == off["f_tasks"]
 
 
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
+def test_copies_ahead(hy, rmat16, algo):
+    """F tasks copied ahead at the end of an iteration ("f_ahead") for the
+    next one give the same results; the next iterations run some tasks from
+    those copies, and each copy ahead is counted in the F link bytes.  The
+    engine is run twice, so the second run starts with the first one's
+    slots and ring position, and once with the device loop off."""
+    # one partition per task and a staging share that holds several slots (a
+    # copy ahead needs a slot beyond the ones in use; on R-MAT 16 the first
+    # 32 vertices, one partition, hold about 100 K edges)
+    if algo == "pagerank":
+        g, pb, budget, sf = rmat16, 64 * 1024, edge_bytes(rmat16, algo), 0.75
+    else:
+        g = gg.mesh(256, 128, shortcut_frac=0.0, wmax=1000)
+        pb, budget, sf = 16384, edge_bytes(g, algo) // 2, 0.5
+    src = None if algo == "pagerank" else 0
+    base = engine(hy, g, budget, part_bytes=pb, force_route=2, k=1, staging_frac=sf)
+    ref = base.run(algo, src)
+    ref_st = base.stats()
+    assert base.info()["n_slots"] >= 4
+    base.close()
+    for loop in (1, 0):
+        e = engine(hy, g, budget, part_bytes=pb, force_route=2, k=1, staging_frac=sf, f_ahead=3,
+                   device_loop=loop)
+        assert e.get_param("f_ahead") == 3
+        for _ in range(2):
+            got = e.run(algo, src)
+            check(g, algo, got)
+            st = e.stats()
+            assert st["f_ahead_tasks"] > 0 and st["f_ahead_hits"] > 0
+            assert st["f_ahead_hits"] <= st["f_ahead_tasks"]
+            if algo != "pagerank":
+                assert np.array_equal(got, ref)
+                # the same F sets per iteration (min-updates): tasks run from a
+                # copy ahead are not copied again, and copies ahead count as F bytes
+                assert st["f_tasks"] == ref_st["f_tasks"]
+                missed = st["link_bytes"][2] - ref_st["link_bytes"][2]
+                assert missed >= 0
+        e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank", "cc"])
+def test_copy_kernel(hy, rmat16, rmat16_sym, algo):
+    """F copies by a kernel over mapped host memory ("f_copy" blocks per SM)
+    in place of the copy engine give the same results, alone and with copies
+    ahead.  The kernel starts at the 16-byte boundary at or below a task's
+    first edge, so it reads at most 3 words more per array and task."""
+    g = rmat16_sym if algo == "cc" else rmat16
+    src = None if algo in ("pagerank", "cc") else 0
+    narr = 2 if algo == "sssp" else 1
+    runs = {}
+    for fc, fa in ((0, 0), (2, 0), (1, 2)):
+        e = engine(hy, g, edge_bytes(g, algo), force_route=2, k=1, staging_frac=0.75, f_copy=fc, f_ahead=fa)
+        assert e.get_param("f_copy") == fc
+        got = e.run(algo, src)
+        check(g, algo, got)
+        runs[(fc, fa)] = (got, e.stats())
+        e.close()
+    ref, st0 = runs[(0, 0)]
+    got, st = runs[(2, 0)]
+    if algo != "pagerank":
+        assert np.array_equal(got, ref)
+        assert st["f_tasks"] == st0["f_tasks"]
+        extra = st["link_bytes"][2] - st0["link_bytes"][2]
+        assert 0 <= extra <= 3 * 4 * narr * st["f_tasks"]
+    assert st["kernel_launches"] > st0["kernel_launches"]
+
+
 def test_sssp_overflow(hy):
     g = gg.CSR(4, 3, np.array([0, 1, 2, 3, 3], np.uint64), np.array([1, 2, 3], np.uint32),
                np.array([0x7FFFFFFF, 0x7FFFFFFF, 5], np.uint32))
