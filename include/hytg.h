@@ -237,7 +237,12 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * not in kernel_ms or the timeline; if the installed CUDA driver cannot build
  * the graph, the context keeps using the host loop and graph_launches stays
  * 0 (and if it cannot hold the F and C nodes, those iterations go to the
- * host as at 1), "serve_frames" (serving:
+ * host as at 1), "loop_after_fc" (0, default: in single-source PageRank and
+ * PPR runs whose graph holds no F and C nodes, the iteration after one with
+ * F or C work is planned by the host at once, and the device loop takes
+ * over after an iteration without such work; 1, and always for the other
+ * algorithms: the device loop is entered after every host-issued iteration),
+ * "serve_frames" (serving:
  * cap on the query frames hytg_serve_begin plans, 0 (default): as many as
  * the slots can use; see hytg_serve_get_info), "batch_sparse_below" (batched
  * SSSP relax: a warp whose 32 edges carry fewer active sources per edge

@@ -108,6 +108,32 @@ __device__ __forceinline__ unsigned long long warp_scan_u64(unsigned long long x
     return x;
 }
 
+// Warp sum of values below 2^43 with two 32-bit warp reductions: the low
+// 16 bits of 32 lanes sum below 2^21 and the bits above below 2^32, so both
+// halves are exact.  (Degrees and line counts are below E, and the
+// PageRank priority is capped at 2^40.)  Needs all 32 lanes.
+__device__ __forceinline__ unsigned long long warp_sum_lt43(unsigned long long x) {
+    const unsigned int lo = __reduce_add_sync(0xffffffffu, (unsigned int)(x & 0xFFFFull));
+    const unsigned int hi = __reduce_add_sync(0xffffffffu, (unsigned int)(x >> 16));
+    return ((unsigned long long)hi << 16) + lo;
+}
+
+// Inclusive warp scan in 32-bit arithmetic when every lane's value is below
+// 2^27 (the warp's total then stays below 2^32), else in 64-bit.
+__device__ __forceinline__ unsigned long long warp_scan_small(unsigned long long x) {
+    if (__all_sync(0xffffffffu, x < (1ull << 27))) {
+        const int lane = threadIdx.x & 31;
+        unsigned int y = (unsigned int)x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        return y;
+    }
+    return warp_scan_u64(x);
+}
+
 // Counter-based mix used only for the "random route" test mode.
 __host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
     x ^= x >> 33; x *= 0xff51afd7ed558ccdull;

@@ -251,6 +251,8 @@ struct hytg_ctx {
     double compact_host = 0;                             // C route compacted by this many host threads (0: GPU gather)
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
+    double loop_after_fc = 0;                            // 1: enter the device loop right after an F/C iteration
+    bool last_fc = false;                                // the last host-issued iteration had F or C work
     double host_huge = 0;                                // 1: edge arrays in transparent huge pages, registered
     double serve_frames_param = 0;                       // serving: cap on query frames (0: what the slots need)
     double batch_sparse_below = -1;                      // batched SSSP/PPR relax path switch (sources per
@@ -1622,6 +1624,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     // hold their slots.
     const uint32_t n_fs = std::max<uint32_t>(1, std::min<uint32_t>(cv.n_slots, (uint32_t)c->streams));
     uint32_t rr = ahead ? c->ring_pos : 0;
+    int last_copied = -1;                     // slot of this iteration's last copy
     // An F copy by the copy engine moves the task's edges exactly; the copy
     // kernel ("f_copy" > 0) starts at the 16-byte boundary at or below the
     // first edge, so the slot then holds up to 3 words before it (when it has
@@ -1678,6 +1681,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             }
             CK(cudaEventRecord(c->ev_copied[slot], cs));
             c->slot_held[slot] = {i0, j, n_arrays};
+            last_copied = (int)slot;
         } else if (ahead) {
             // copied ahead: its bytes were counted when the copy was issued
             c->stats.f_ahead_hits += 1;
@@ -1763,9 +1767,13 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     for (uint32_t sl = 0; sl < (uint32_t)kMaxSlots; ++sl)
         if ((missed >> sl) & 1u) CK(cudaStreamWaitEvent(c->s_main, c->ev_copied[sl], 0));
     // --- copies ahead for the next iteration: this iteration's first tasks,
-    // into the least recently used slots of the ring; each waits only for
-    // its slot's last relax, and the main stream does not wait for them
+    // into the least recently used slots of the ring.  Each waits for its
+    // slot's last relax and for this iteration's last copy, so that it runs
+    // in the gap that the iteration's last relaxes and the next planning
+    // leave on the link, not among this iteration's copies; the main stream
+    // does not wait for them.
     if (ahead && !tasks.empty()) {
+        cudaEvent_t after = last_copied >= 0 ? c->ev_copied[last_copied] : nullptr;
         const uint32_t n_ahead = std::min<uint32_t>({(uint32_t)c->f_ahead, cv.n_slots - 1, (uint32_t)order.size()});
         for (uint32_t q = 0; q < n_ahead; ++q) {
             const FTask &ft = tasks[order[q]];
@@ -1774,6 +1782,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
             cudaStream_t cs = c->s_cp[slot];
             c->slot_held[slot] = hytg_ctx::SlotHeld();
             CK(cudaStreamWaitEvent(cs, c->ev_free[slot], 0));
+            if (after) CK(cudaStreamWaitEvent(cs, after, 0));
             const uint64_t words = e0 + ft.edges - base_of(e0, ft.edges);
             {
                 ScopedTime t(c, HYTG_K_COPY_F, cs);
@@ -1812,6 +1821,7 @@ hytg_status issue_work(hytg_ctx *c, int algo, unsigned int bucket, const char *h
     c->stats.link_bytes[kRouteZ] += zb;
     c->stats.link_bytes[kRouteC] += cbts;
     c->stats.f_tasks += n_tasks;
+    c->last_fc = n_tasks > 0 || c_edges > 0;
     c->stats.edges_relaxed += act_edges;
     c->stats.vertices_processed += hs->n_active;
     rec.active_edges = act_edges;
@@ -2221,6 +2231,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "compact_host") { if (v < 0 || v > 256 || v != std::floor(v)) return bad(); c->compact_host = v; }
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
     else if (k == "device_loop") { if (v != 0 && v != 1 && v != 2) return bad(); c->device_loop = v; }
+    else if (k == "loop_after_fc") { if (v != 0 && v != 1) return bad(); c->loop_after_fc = v; }
     else if (k == "host_huge") { if (v != 0 && v != 1) return bad(); c->host_huge = v; }
     else if (k == "serve_frames") { if (v < 0 || v > kMaxFrames || v != std::floor(v)) return bad(); c->serve_frames_param = v; }
     else if (k == "batch_sparse_below") { if (v < -1 || v > 65 || v != std::floor(v)) return bad(); c->batch_sparse_below = v; }
@@ -2260,6 +2271,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "compact_host") *v = c->compact_host;
     else if (k == "priority") *v = c->priority;
     else if (k == "device_loop") *v = c->device_loop;
+    else if (k == "loop_after_fc") *v = c->loop_after_fc;
     else if (k == "host_huge") *v = c->host_huge;
     else if (k == "serve_frames") *v = c->serve_frames_param;
     else if (k == "batch_sparse_below") *v = c->batch_sparse_below;
@@ -2385,7 +2397,16 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
             if (s != HYTG_OK) return s;
             // --- next iteration
             ++it;
-            if (use_loop && !c->loop_unavailable) {
+            // In PageRank's dense phase an iteration with F or C work is
+            // followed by another, so unless the graph holds F and C nodes
+            // the host plans it at once: entering the device loop would only
+            // plan it there, return, and put a host round trip between the
+            // iterations.  After a cache/Z-only iteration the device loop
+            // takes over.  (BFS, SSSP and CC have short F phases; their next
+            // iteration is often cache/Z only and runs best in the graph.)
+            const bool plan_on_host = (algo == kPR || algo == kPPR) && c->last_fc && c->loop_after_fc == 0 &&
+                                      !loop_fc_wanted(c);
+            if (use_loop && !c->loop_unavailable && !plan_on_host) {
                 // captured after iteration 0 has run, so every launcher's
                 // one-time set-up happened outside the capture; a CUDA driver that
                 // cannot build the graph leaves this context on the host loop
@@ -2395,7 +2416,7 @@ hytg_status hytg_run(hytg_ctx *c, hytg_algo algo_in, const uint32_t *sources, ui
                     cudaGetLastError();
                 }
             }
-            if (use_loop && !c->loop_unavailable) {
+            if (use_loop && !c->loop_unavailable && !plan_on_host) {
                 // iterations on the device until one needs the F or C route
                 int status = 0;
                 s = run_device_loop(c, it, bucket, delta, status);

@@ -114,17 +114,34 @@ __global__ void k_cc_write(AlgoState st, unsigned long long V, const unsigned in
         out[st.perm ? st.perm[v] : v] = tmp[st.val[v]];
 }
 
-// Fold the per-SM hub replicas into delta and clear them.
-__global__ void k_hub_reduce(AlgoState st) {
+// Fold the per-SM hub replicas into delta and clear them.  A block takes 32
+// consecutive hub ids; each of its 8 warps sums every 8th replica row of
+// those ids (128-byte rows, eight loads in flight), and the first warp adds
+// the 8 partial sums into delta.
+__global__ void __launch_bounds__(256) k_hub_reduce(AlgoState st) {
+    __shared__ float part[8][32];
     const unsigned int K = st.n_hub_rep;
-    for (unsigned int v = blockIdx.x * blockDim.x + threadIdx.x; v < K; v += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (unsigned int v0 = blockIdx.x * 32u; v0 < K; v0 += gridDim.x * 32u) {
+        const unsigned int v = v0 + lane;
         float s = 0.0f;
-        for (unsigned int r = 0; r < kHubReplicas; ++r) {
-            float *p = st.hub_rep + (size_t)r * K + v;
-            s += *p;
-            *p = 0.0f;
+        if (v < K) {
+#pragma unroll 8
+            for (unsigned int r = wid; r < kHubReplicas; r += 8) {
+                float *p = st.hub_rep + (size_t)r * K + v;
+                s += *p;
+                *p = 0.0f;
+            }
         }
-        st.delta[v] += s;
+        part[wid][lane] = s;
+        __syncthreads();
+        if (wid == 0 && v < K) {
+            float t = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t += part[q][lane];
+            st.delta[v] += t;
+        }
+        __syncthreads();
     }
 }
 
@@ -352,7 +369,7 @@ cudaError_t launch_pr_finalize(const AlgoState &st, unsigned long long V, float 
 
 cudaError_t launch_hub_reduce(const AlgoState &st, cudaStream_t s) {
     if (!st.hub_rep || st.n_hub_rep == 0) return cudaSuccess;
-    k_hub_reduce<<<(st.n_hub_rep + 255) / 256, 256, 0, s>>>(st);
+    k_hub_reduce<<<(st.n_hub_rep + 31) / 32, 256, 0, s>>>(st);
     return cudaGetLastError();
 }
 

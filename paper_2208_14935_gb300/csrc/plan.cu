@@ -158,13 +158,13 @@ __global__ void __launch_bounds__(256) k_count(GraphDev g, AlgoState st, PartArr
                     (unsigned long long)st.n_arrays * lines_spanned(o0[q] * 4ull, deg * 4ull, m);
                 a_nact += __popc(elig);
                 a_ent += __popc(__ballot_sync(0xffffffffu, deg > 0));
-                a_edges += warp_sum_u64(deg);
-                a_lines += warp_sum_u64(ln);
+                a_edges += warp_sum_lt43(deg);
+                a_lines += warp_sum_lt43(ln);
                 if (st.prio) {
                     // |delta| in units of 2^-24, capped at 2^40 per vertex; the
                     // sum only orders the F tasks, so rounding cannot matter
                     const float x = fminf(fabsf(dl[q]) * 16777216.f, 1099511627776.f);
-                    a_prio += warp_sum_u64(act ? (unsigned long long)x : 0ull);
+                    a_prio += warp_sum_lt43(act ? (unsigned long long)x : 0ull);
                 }
             }
         }
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256) k_bin(GraphDev g, AlgoState st, PartArray
                     }
                 }
                 const unsigned int bal = __ballot_sync(0xffffffffu, deg > 0);
-                const unsigned long long incl = warp_scan_u64(deg);
+                const unsigned long long incl = warp_scan_small(deg);
                 const unsigned long long w_edges = __shfl_sync(0xffffffffu, incl, 31);
                 unsigned long long old = 0;
                 if (lane == 0 && bal)

@@ -197,3 +197,32 @@ def test_run_deadline(hy, loop):
     e.set_param("run_timeout_ms", 60000)         # a deadline far away changes nothing
     assert np.array_equal(e.run("bfs", 0), got)
     e.close()
+
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
+def test_loop_after_fc(hy, rmat16, algo):
+    """Whether the host plans PageRank's iteration after one with F or C
+    work ("loop_after_fc" 0, the default) or the device loop takes over after
+    every host iteration (1), the results are the same, and for BFS/SSSP
+    (which always take the device loop) so are the iterations and the edges
+    relaxed; the mesh still runs iterations in the graph."""
+    src = None if algo == "pagerank" else 0
+    runs = {}
+    for v in (0, 1):
+        e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, loop_after_fc=v)
+        assert e.get_param("loop_after_fc") == v
+        got = e.run(algo, src)
+        check(rmat16, algo, got, 0)
+        runs[v] = (got, e.stats())
+        e.close()
+    if algo != "pagerank":
+        assert np.array_equal(runs[0][0], runs[1][0])
+        assert runs[0][1]["iterations"] == runs[1][1]["iterations"]
+        assert runs[0][1]["edges_relaxed"] == runs[1][1]["edges_relaxed"]
+    g = gg.mesh(200, 100, shortcut_frac=0.001, radius=8, wmax=1000)
+    if algo != "pagerank":
+        e = engine(hy, g, g.E * 8 // 5, part_bytes=16384)
+        check(g, algo, e.run(algo, 0), 0)
+        st = e.stats()
+        assert st["graph_iterations"] > 0, st
+        e.close()

@@ -189,10 +189,11 @@ def test_partition_table_matches_oracle(hy, rmat16, hub_frac):
         e.close()
 
 
-@pytest.mark.parametrize("algo", ["bfs", "sssp"])
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "pagerank"])
 def test_planner_matches_oracle(hy, rmat16, algo):
     """Cost analysis and engine selection on the device (Alg. 1) against the
-    exact-rational oracle, on random frontiers of several densities."""
+    exact-rational oracle, on random frontiers of several densities
+    (PageRank's planning walks the bitmap with the dense mapping)."""
     params = dict(alpha=0.8, beta=0.4, gamma=0.625, MR=8)
     e = engine(hy, rmat16, edge_bytes(rmat16, algo) // 4, **params)
     vb = e.partitions()
