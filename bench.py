@@ -411,10 +411,31 @@ def union_ms(iv):
     return busy
 
 
+def copy_boundaries(tl, min_gap_ms=0.1):
+    """The F copies' share of a run: the time the copy engine was busy (union
+    of the copy intervals) and the idle stretches between copies.  Copies
+    of one iteration run back to back, a few microseconds apart; a stretch
+    longer than min_gap_ms is mostly the boundary between two iterations
+    that copy (the last tasks' relaxes, then the next planning), sometimes a
+    copy waiting for its staging slot.  Returns the busy time, the number of
+    such stretches and their mean length."""
+    cp = tl["kind"] == 8
+    order = np.argsort(tl["start_ms"][cp], kind="stable")
+    cs, ce = tl["start_ms"][cp][order], tl["end_ms"][cp][order]
+    gaps, end = [], None
+    for a, b in zip(cs, ce):
+        if end is not None and a - end > min_gap_ms:
+            gaps.append(float(a - end))
+        end = b if end is None else max(end, b)
+    return {"copy_busy_ms": union_ms(list(zip(cs, ce))), "idle_stretches": len(gaps),
+            "idle_stretch_ms": float(np.mean(gaps)) if gaps else None}
+
+
 def timeline_summary(tl, hytg):
     """Per-run figures from the launch timeline: every F copy's rate, the wall
-    time during which any route moved host-link bytes, and per-launch edge
-    counts and durations of the two PageRank kernels."""
+    time during which any route moved host-link bytes, per-launch edge
+    counts and durations of the two PageRank kernels, and the copies' share
+    of each iteration (copy_boundaries)."""
     dur = tl["end_ms"] - tl["start_ms"]
     cp = tl["kind"] == 8
     link = np.isin(tl["kind"], LINK_KINDS)
@@ -425,7 +446,8 @@ def timeline_summary(tl, hytg):
             "link_busy_ms": union_ms(list(zip(tl["start_ms"][link], tl["end_ms"][link]))),
             "sp_n": int(sp.sum()), "sp_ms": float(dur[sp].sum()), "sp_edges": int(tl["edges"][sp].sum()),
             "sp_vertices": int(tl["vertices"][sp].sum()),
-            "rf_n": int(rf.sum()), "rf_ms": float(dur[rf].sum()), "rf_edges": int(tl["edges"][rf].sum())}
+            "rf_n": int(rf.sum()), "rf_ms": float(dur[rf].sum()), "rf_edges": int(tl["edges"][rf].sum()),
+            **copy_boundaries(tl)}
 
 
 def pct(xs, q):
@@ -546,6 +568,12 @@ def main():
             busy = sum(p[a]["tl"]["link_busy_ms"] for p in steps)
             d["link_busy_frac"] = busy / ms
             d["link_frac_while_busy"] = lb / (busy * 1e-3) / 1e9 / probe if busy > 0 else None
+            # the copy engine's share of the run and its idle stretches
+            # (mostly the boundaries of the iterations that copy)
+            d["copy_busy_frac"] = sum(p[a]["tl"]["copy_busy_ms"] for p in steps) / ms
+            d["copy_idle_stretches"] = steps[-1][a]["tl"]["idle_stretches"]
+            gaps = [p[a]["tl"]["idle_stretch_ms"] for p in steps if p[a]["tl"]["idle_stretch_ms"] is not None]
+            d["copy_idle_stretch_ms"] = float(np.mean(gaps)) if gaps else None
         if a == "pagerank":
             # a-posteriori bound on the L1 error of the normalised ranks:
             # sum |delta| left / ((1 - d) * sum rank)

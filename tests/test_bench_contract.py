@@ -29,3 +29,20 @@ def test_reference_arm_line():
     assert all(p["steps"] == 1 and p["gteps"] > 0 for p in d["cpu_baseline"]["per_algo"].values())
     cfg = d["config"]
     assert cfg["workload"].startswith("rmat12 ") and cfg["V"] == 4096 and cfg["E"] == 65536
+
+
+def test_copy_boundaries():
+    """The copy engine's busy time is the union of the copy intervals, and
+    idle stretches are counted only past the threshold."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    dt = np.dtype([("kind", np.uint32), ("start_ms", np.float64), ("end_ms", np.float64)])
+    rows = [(8, 0.0, 1.0), (8, 0.5, 1.5), (4, 1.0, 3.0), (8, 1.52, 2.0),   # back to back
+            (8, 2.6, 3.0), (7, 3.0, 3.1), (8, 3.05, 4.0), (8, 4.3, 5.0)]   # gaps 0.6, 0.05, 0.3
+    tl = np.array(rows, dtype=dt)
+    r = bench.copy_boundaries(tl, min_gap_ms=0.1)
+    assert abs(r["copy_busy_ms"] - (1.5 + 0.48 + 0.4 + 0.95 + 0.7)) < 1e-9
+    assert r["idle_stretches"] == 2 and abs(r["idle_stretch_ms"] - 0.45) < 1e-9
+    assert bench.copy_boundaries(tl[:2])["idle_stretch_ms"] is None
+    assert bench.union_ms([(0, 2), (1, 3), (5, 6)]) == 4
