@@ -32,6 +32,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "hytg.h"
 
@@ -727,8 +729,15 @@ int stream_index(const hytg_ctx *c, cudaStream_t s) {
     return 0;
 }
 
+// NVTX range names of the launch kinds (index: HYTG_K_*, then the second
+// pass), so that a profiler can select a route's launches; without a tool
+// attached the NVTX calls do nothing.
+const char *const kKindName[] = {"init", "count", "bin", "relax_cache", "relax_F", "gather_C", "relax_C",
+                                 "relax_Z", "copy_F", "final", "cache_fill", "other", "second_pass"};
+
 // CUDA-event interval of one launch (timing on); bytes, edges, vertices and
 // the second-pass counter slot are filled in by the caller when they apply.
+// Every host-issued launch is also an NVTX range named for its kind.
 struct ScopedTime {
     hytg_ctx *c;
     int kind;
@@ -737,6 +746,7 @@ struct ScopedTime {
     uint64_t bytes = 0, edges = 0, vertices = 0;
     int sp_slot = -1;
     uint32_t part_first = 0, part_last = 0;
+    bool pushed = false;
     ScopedTime(hytg_ctx *c_, int kind_, cudaStream_t s_, bool kernel = true) : c(c_), kind(kind_), s(s_) {
         const unsigned k = (kernel && kind != HYTG_K_COPY_F && kind != HYTG_K_CACHE_FILL) ? 1 : 0;
         if (c->capturing) {              // inside a graph body: counted per body run
@@ -744,12 +754,15 @@ struct ScopedTime {
             return;
         }
         c->stats.kernel_launches += k;
+        nvtxRangePushA(kind >= 0 && kind <= kKindSecondPass ? kKindName[kind] : "launch");
+        pushed = true;
         if (c->timing != 0) {
             a = pool_event(c);
             cudaEventRecord(a, s);
         }
     }
     ~ScopedTime() {
+        if (pushed) nvtxRangePop();
         if (a) {
             cudaEvent_t b = pool_event(c);
             cudaEventRecord(b, s);
