@@ -242,7 +242,9 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * F or C work is planned by the host at once, and the device loop takes
  * over after an iteration without such work; 1, and always for the other
  * algorithms: the device loop is entered after every host-issued iteration),
- * "serve_frames" (serving:
+ * "z_blocks" (blocks per SM of a host-issued zero-copy relax, 1..32,
+ * default 12: more blocks than fit at once keep more host-link reads in
+ * flight beside the other streams' kernels), "serve_frames" (serving:
  * cap on the query frames hytg_serve_begin plans, 0 (default): as many as
  * the slots can use; see hytg_serve_get_info), "batch_sparse_below" (batched
  * SSSP relax: a warp whose 32 edges carry fewer active sources per edge

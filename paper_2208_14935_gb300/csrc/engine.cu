@@ -254,6 +254,7 @@ struct hytg_ctx {
     double priority = 1;                                 // Sec. VI-A: F tasks in delta-first order (PageRank/PPR)
     double device_loop = 1;                              // cache/Z-only iterations inside a CUDA graph
     double loop_after_fc = 0;                            // 1: enter the device loop right after an F/C iteration
+    double z_blocks = 12;                                // zero-copy relax (host-issued): blocks per SM
     bool last_fc = false;                                // the last host-issued iteration had F or C work
     double host_huge = 0;                                // 1: edge arrays in transparent huge pages, registered
     double serve_frames_param = 0;                       // serving: cap on query frames (0: what the slots need)
@@ -1137,7 +1138,7 @@ hytg_status issue_plan_tail(hytg_ctx *c, int algo, unsigned int bucket, cudaStre
         t.route = kRouteZ; t.mode = kModeHost; t.dst = c->m_dst; t.w = c->m_w; t.shift = 0;
         t.device_sized = true; t.src_len = c->E; t.link_ctr = c->d_link_ctr + 2 * kRouteZ;
         ScopedTime tm(c, HYTG_K_RELAX_Z, s);
-        CK(relax_any(c, st, la, sum, t, cap, s));
+        CK(relax_any(c, st, la, sum, t, (int)c->z_blocks * (int)device_sms(), s));
     }
     return HYTG_OK;
 }
@@ -2245,6 +2246,7 @@ hytg_status hytg_set_param(hytg_ctx *c, const char *key, double v) {
     else if (k == "priority") { if (v != 0 && v != 1) return bad(); c->priority = v; }
     else if (k == "device_loop") { if (v != 0 && v != 1 && v != 2) return bad(); c->device_loop = v; }
     else if (k == "loop_after_fc") { if (v != 0 && v != 1) return bad(); c->loop_after_fc = v; }
+    else if (k == "z_blocks") { if (v < 1 || v > 32 || v != std::floor(v)) return bad(); c->z_blocks = v; }
     else if (k == "host_huge") { if (v != 0 && v != 1) return bad(); c->host_huge = v; }
     else if (k == "serve_frames") { if (v < 0 || v > kMaxFrames || v != std::floor(v)) return bad(); c->serve_frames_param = v; }
     else if (k == "batch_sparse_below") { if (v < -1 || v > 65 || v != std::floor(v)) return bad(); c->batch_sparse_below = v; }
@@ -2285,6 +2287,7 @@ hytg_status hytg_get_param(hytg_ctx *c, const char *key, double *v) {
     else if (k == "priority") *v = c->priority;
     else if (k == "device_loop") *v = c->device_loop;
     else if (k == "loop_after_fc") *v = c->loop_after_fc;
+    else if (k == "z_blocks") *v = c->z_blocks;
     else if (k == "host_huge") *v = c->host_huge;
     else if (k == "serve_frames") *v = c->serve_frames_param;
     else if (k == "batch_sparse_below") *v = c->batch_sparse_below;
