@@ -203,6 +203,11 @@ hytg_status hytg_set_device_budget(hytg_ctx *ctx, uint64_t bytes);
  * relaxes and the next planning; a next-iteration task found among them runs
  * from its slot, in its place in the order; counted in f_ahead_tasks /
  * f_ahead_hits; when on, "slot_reuse" is not applied; 0: off),
+ * "f_copy" (0, default: F copies by the copy engine, cudaMemcpyAsync; n in
+ * 1..32: by a kernel with n blocks per SM that reads the task's edges from
+ * mapped host memory with 16-byte loads, starting at the 16-byte boundary
+ * at or below the first edge when the slot has room for the up to 3 extra
+ * words read, else by the copy engine),
  * "timing" (1: CUDA-event time per kernel
  * kind), "hub_frac" (fraction of vertices moved to the front by hub sorting
  * at the next hytg_load_csr, Sec. VI-A; 0 disables it; default 0.08),
